@@ -1,0 +1,335 @@
+"""Benchmark of the fused two-component TSSP step on GB300.
+
+Workload (one "step" = one Strang step S(dt) of Sec. 3.2 over the whole batch):
+B independent instances of the 256 x 256 real-time problem (box [-10,10]^2,
+harmonic trap, Raman coupling Omega = 2, detuning delta = 0.5 y, kL = 1,
+g11 = g22 = g12 = 200, dt = 5e-4, complex64), each started from the ground
+state of the 64 x 64 two-component problem (g = 100/100/95) upsampled
+spectrally to 256^2 with seeded phase noise per instance.  With B = 256 the
+batch is 256 MiB, twice the L2 size, so every timed step streams from HBM
+(no L2 flush needed).
+
+Prints one JSON line: grid-point-steps/s (points of one component x steps x
+instances, the paper's N of Sec. 5), the roofline of the dominant kernel, the
+end-to-end figure through the C ABI with host buffers, the CPU oracle timed on
+the host cores, and the SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(one instance per step, a bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2010_15069_gb300 import inputs  # noqa: E402
+
+NX = NY = 256
+DT = 5e-4
+DEFAULT_INSTANCES = 256
+BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}  # read + write both components, one pass
+PASSES_PER_STEP = 2
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ inputs
+
+def ground_state_gpu():
+    """Ground state of the 64^2 problem computed by this library (c128)."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    p = inputs.config0()
+    with sp.Context(64, 64, 10.0, 10.0, "c128") as c:
+        c.set_potentials(p.V, p.delta, p.Omega, p.g11, p.g22, p.g12, p.kL)
+        t = torch.from_numpy(inputs.gaussian_spinor(p.grid, seed=0)).cuda()
+        c.step_imag(t, 1e-3, 2000, 1, (0.5, 0.5))
+        torch.cuda.synchronize()
+        return t.cpu().numpy()
+
+
+def initial_states(B, ground):
+    base = inputs.upsample_spectral(ground, NX, NY)
+
+    def psi0(i):
+        ph = 1e-3 * (2.0 * inputs.uniform01(1000 + i, 2 * NX * NY) - 1.0)
+        return base * np.exp(1j * ph.reshape(2, NY, NX))
+    return psi0
+
+
+def make_workload(B, dtype="c64", ground=None, stream=None):
+    """(context, device batch tensor, psi0(i)) of the benchmark workload."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    if ground is None:
+        ground = ground_state_gpu()
+    psi0 = initial_states(B, ground)
+    p = inputs.config1(NX)
+    c = sp.Context(NX, NY, 10.0, 10.0, dtype, ninst=B, stream=stream)
+    c.set_potentials_separable(-1, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+    npt = np.complex64 if dtype == "c64" else np.complex128
+    host = np.empty((B, 2, NY, NX), dtype=npt)
+    for i in range(B):
+        host[i] = psi0(i)
+    t = torch.from_numpy(host).cuda()
+    torch.cuda.synchronize()
+    return c, t, psi0
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.rows = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        under_load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(under_load) if under_load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_rate(budget_s=12.0, max_steps=400):
+    """The FP64 oracle on one instance of the workload: (pt-steps/s, steps, seconds)."""
+    import oracle
+    p = inputs.config1(NX)
+    m = oracle.Model(NX, NY, 10.0, 10.0, V=p.V, delta=p.delta, Omega=p.Omega,
+                     g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+    psi = inputs.gaussian_spinor(p.grid, seed=0)
+    t0 = time.perf_counter()
+    psi = m.step(psi, DT, 1)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    m.step(psi, DT, n)
+    dt = time.perf_counter() - t0
+    return NX * NY * n / dt, n, dt
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    p = inputs.config1(NX)
+    m = oracle.Model(NX, NY, 10.0, 10.0, V=p.V, delta=p.delta, Omega=p.Omega,
+                     g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+    psi = inputs.gaussian_spinor(p.grid, seed=0)
+    psi = m.step(psi, DT, args.warmup)
+    t0 = time.perf_counter()
+    m.step(psi, DT, args.steps)
+    el = time.perf_counter() - t0
+    value = NX * NY * args.steps / el
+    line = {
+        "impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "pt-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.instances, args.dtype),
+        "cpu_baseline": {"value": value, "unit": "pt-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one 256x256 instance of the batch, {args.steps} Strang steps"},
+        "e2e": {"value": value, "unit": "pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(B, dtype):
+    return {"workload": f"256x256 real-time two-component GPE x {B} instances (Omega=2, delta=0.5y, kL=1, "
+                        f"g=200, dt=5e-4), {dtype}",
+            "grid": [NX, NY], "instances": B, "dt": DT, "box": [-10.0, 10.0],
+            "l2": "batch larger than L2 (no flush)" if B * NX * NY * 16 > 129e6 else "L2-resident batch",
+            "parallelism": "instances sharded per GPU"}
+
+
+def run_fused(args):
+    import torch
+    import paper_2010_15069_gb300 as sp
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B, dtype = args.instances, args.dtype
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        c, t, _ = make_workload(B, dtype, stream=stream)
+    pts = B * NX * NY
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    c.step_real(t, DT, args.warmup)
+    barrier()
+    # timed region: K steps in one call (the steady-state cost of a long run)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        start.record(stream)
+        c.step_real(t, DT, args.steps)
+        stop.record(stream)
+        launches = c.last_launches()
+        barrier()
+    ms = start.elapsed_time(stop)
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * pts * args.steps / (ms * 1e-3)
+
+    # per-kernel event timing over a second run of the same timed region
+    c.set_timing(True)
+    c.step_real(t, DT, args.steps)
+    kt = c.timing()
+    c.set_timing(False)
+    kinds = {k: v for k, v in kt.items() if k.startswith(("row_real_fused", "col_real"))}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    n_dom, ms_dom = kinds[dom]
+    avg_s = ms_dom * 1e-3 / n_dom
+    alg_bytes = BYTES_PER_PT_PASS[dtype] * pts
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / avg_s / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                traffic = json.load(f).get(f"{dom}:{dtype}:{B}")
+        except (OSError, ValueError):
+            traffic = None
+
+    # end to end through the C ABI with pinned host buffers: H2D, one step, D2H
+    host = torch.empty(tuple(t.shape), dtype=t.dtype, pin_memory=True)
+    host.copy_(t)
+    hnp = host.numpy()
+    c.step_real(hnp, DT, 1)
+    e2e_steps = max(3, min(args.steps, 20))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        c.step_real(hnp, DT, 1)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * pts * e2e_steps / e2e_s
+    psi_bytes = t.numel() * t.element_size()
+    c.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1:
+        rate, n, el = oracle_rate()
+        cpu = {"value": rate, "unit": "pt-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"one 256x256 instance, {n} FP64 Strang steps in {el:.1f} s (single thread)"}
+    line = {
+        "metric": "grid-point-steps/s", "value": value, "unit": "pt-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
+        "config": workload_config(B, dtype),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
+                     "peak_source": peak_kind,
+                     "step_frac": (PASSES_PER_STEP * alg_bytes * args.steps / (ms * 1e-3) / 1e9) / peak},
+        "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kt.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "pt-steps/s", "h2d_bytes_per_step": psi_bytes,
+                "d2h_bytes_per_step": psi_bytes, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["fused", "reference"], default="fused")
+    ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2010_15069_gb300 import build
+        build.build()
+        run_fused(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * spgpe.h -- C ABI of the GB300 (sm_103a) time-splitting spectral solver for
+ * the two-component quasi-2D Gross-Pitaevskii equation of arXiv:2010.15069.
+ *
+ * Model (Eq. 3 signs, hbar = m = omega_perp = 1; Eqs. 4-8 split it into the
+ * kinetic H(1), potential H(2), interaction H(3) and Raman H(4) parts):
+ *
+ *   i dPsi/dt = H Psi,  Psi = (psi_up, psi_dn),
+ *   H = diag(T_up, T_dn)(k) + V 1 + (delta/2) sigma_z + (Omega/2) sigma_x
+ *       + diag(g11 rho_up + g12 rho_dn, g22 rho_dn + g12 rho_up),
+ *   T_up(k) = k^2/2 - kL kx,   T_dn(k) = k^2/2 + kL kx,   rho_j = |psi_j|^2.
+ *
+ * Grid (Sec. 3.2): x_i = -xmax + i dx, dx = 2 xmax / nx (periodic, +xmax
+ * excluded), kx = 2 pi fftfreq(nx, dx) with the Nyquist bin at -pi/dx; the
+ * same in y.  nx and ny are powers of two in [8, 4096].
+ *
+ * One step (Eq. 13 operators, Strang splitting of Sec. 3.2, four 2D FFTs):
+ *   S(dt) = R(dt/2) F^-1 K(dt) F R(dt/2),   R(tau) = X(tau/2) D(tau) X(tau/2),
+ *   D(tau): psi_up *= exp(-i tau (V + delta/2 + g11 rho_up + g12 rho_dn)),
+ *           psi_dn *= exp(-i tau (V - delta/2 + g22 rho_dn + g12 rho_up)),
+ *           densities taken on entry to D;
+ *   X(tau) = exp(-i tau Omega sigma_x / 2);  K(tau): psi_hat_j *= exp(-i tau T_j(k)).
+ * Imaginary time replaces -i tau by -tau in every factor and rescales the
+ * spinor to the target atom number after every step (Sec. 3.2).
+ *
+ * Data layout: a spinor batch is [ninst][2][ny][nx] interleaved complex
+ * (re, im), component up first, x fastest, in the context's precision
+ * (SPGPE_C64: float pairs, SPGPE_C128: double pairs).  Atom numbers are
+ * N_j = dx dy sum |psi_j|^2.
+ *
+ * Ownership and threading: the spinor buffer and the CUDA stream belong to
+ * the caller; tables, twiddles and scratch belong to the context.  A context
+ * is not thread-safe; use one context per stream.  Calls on device buffers
+ * are stream-ordered and asynchronous unless documented as synchronising.
+ *
+ * Errors: every call returns SPGPE_OK (0) or a negative status; nothing is
+ * thrown or aborted across the ABI.  spgpe_last_error() gives a message.
+ */
+#ifndef SPGPE_H
+#define SPGPE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPGPE_VERSION 100
+
+enum { SPGPE_C64 = 1, SPGPE_C128 = 2 };
+enum { SPGPE_NORM_TOTAL = 0, SPGPE_NORM_PER_COMPONENT = 1 };
+enum {
+  SPGPE_OK = 0,
+  SPGPE_EINVAL = -1,     /* bad argument: size, pointer, dtype, non-finite input */
+  SPGPE_ENOMEM = -2,     /* device or host allocation failed */
+  SPGPE_ECUDA = -3,      /* a CUDA runtime call failed; see spgpe_last_error */
+  SPGPE_ENONFINITE = -4, /* a norm or energy reduction met NaN/Inf (or a zero norm) */
+  SPGPE_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  SPGPE_ESTATE = -6      /* call out of order (e.g. stepping before potentials) */
+};
+
+typedef struct spgpe_ctx spgpe_ctx;
+
+/* Create a context for one nx x ny instance over [-xmax, xmax) x [-ymax, ymax)
+ * (Sec. 3.2 grid).  dtype is SPGPE_C64 or SPGPE_C128.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream), borrowed, not owned.  Allocates
+ * the context's device tables.  Returns EINVAL for sizes that are not powers
+ * of two in [8, 4096], non-positive or non-finite extents, or a bad dtype;
+ * ENOMEM / ECUDA on allocation failure.  *out is NULL on failure. */
+int spgpe_init_grid(spgpe_ctx **out, int nx, int ny, double xmax, double ymax,
+                    int dtype, void *cuda_stream);
+
+/* As spgpe_init_grid for a batch of ninst (>= 1) independent instances of the
+ * same grid, each with its own potentials and couplings (parameter sweeps).
+ * The spinor buffer then holds ninst spinors back to back. */
+int spgpe_init_batch(spgpe_ctx **out, int nx, int ny, double xmax, double ymax,
+                     int ninst, int dtype, void *cuda_stream);
+
+/* Potentials and couplings of Eqs. 3-8 for every instance.  V, delta, Omega
+ * are host FP64 arrays [ny][nx] (row-major), NULL meaning zero; they are
+ * copied (the caller may free them on return) and stored in the working
+ * precision.  g11, g22, g12 are the interaction strengths, kL the Raman
+ * recoil momentum of the kL kx sigma_z term.  Synchronises the stream.
+ * Returns EINVAL on a NULL context or any non-finite value. */
+int spgpe_set_potentials(spgpe_ctx *ctx, const double *V, const double *delta,
+                         const double *Omega, double g11, double g22, double g12,
+                         double kL);
+
+/* Separable form of the same call that moves no 2D arrays:
+ * V(x,y) = Vx[ix] + Vy[iy], delta = delta_x[ix] + delta_y[iy],
+ * Omega = Omega_x[ix] + Omega_y[iy]; each pointer is a host FP64 array of
+ * length nx (x pieces) or ny (y pieces), NULL meaning zero.  inst selects the
+ * instance of a batch; inst = -1 sets every instance.  Replaces any 2D arrays
+ * given earlier.  Synchronises the stream.  EINVAL on bad inst or non-finite
+ * values. */
+int spgpe_set_potentials_separable(spgpe_ctx *ctx, int inst, const double *Vx,
+                                   const double *Vy, const double *delta_x,
+                                   const double *delta_y, const double *Omega_x,
+                                   const double *Omega_y, double g11, double g22,
+                                   double g12, double kL);
+
+/* nsteps real-time Strang steps S(dt) in place on psi (Sec. 3.2, Fig. 1
+ * loop).  psi is the caller's [ninst][2][ny][nx] complex buffer in the
+ * context's precision.  A device pointer is updated asynchronously on the
+ * stream; a host pointer is copied in, stepped and copied back before the
+ * call returns (synchronising).  The state on return equals nsteps
+ * applications of S(dt); consecutive R(dt/2) halves are fused only inside
+ * the call, so a run split over several calls gives the same bits.
+ * nsteps = 0 is a no-op.  ESTATE before any set_potentials call. */
+int spgpe_step_real(spgpe_ctx *ctx, void *psi, double dt, int nsteps);
+
+/* nsteps imaginary-time steps (dt -> -i dtau), rescaling after every step to
+ * the target atom numbers (Sec. 3.2): norm_mode SPGPE_NORM_TOTAL scales both
+ * components by sqrt((target[0]+target[1]) / (N_up+N_dn)),
+ * SPGPE_NORM_PER_COMPONENT scales psi_j by sqrt(target[j] / N_j).  target is a
+ * host array of 2 doubles shared by all instances (NULL = {0.5, 0.5}).
+ * residual_out (host, nullable; ninst doubles) receives the discrete-map
+ * residual of the last step, ||Psi_{n+1} - Psi_n||_2 / (dtau ||Psi_n||_2)
+ * over both components; asking for it synchronises.  A NaN/Inf or zero norm
+ * met during the run is reported as ENONFINITE by the next synchronising
+ * call (this one when residual_out is given). */
+int spgpe_step_imag(spgpe_ctx *ctx, void *psi, double dtau, int nsteps, int norm_mode,
+                    const double *target, double *residual_out);
+
+/* Energy functional whose variation is H Psi, per instance:
+ * out[6*i .. 6*i+5] = {E_total, E_kinetic (incl. -kL kx sigma_z), E_trap,
+ * E_detuning, E_Raman, E_interaction}, extensive (divide by the atom number
+ * for per-particle values).  Kinetic part by Parseval on the 2D FFT.  FP64
+ * accumulation; synchronises.  ENONFINITE if any sum is not finite. */
+int spgpe_energy(spgpe_ctx *ctx, const void *psi, double *out);
+
+/* Atom numbers per instance, out[2*i] = N_up, out[2*i+1] = N_dn, FP64
+ * accumulation; synchronises.  ENONFINITE if a sum is not finite. */
+int spgpe_norm(spgpe_ctx *ctx, const void *psi, double *out);
+
+/* Wait for the context's stream and report an error recorded on the device
+ * by an earlier asynchronous step (ENONFINITE), clearing it. */
+int spgpe_sync(spgpe_ctx *ctx);
+
+/* Comparator with the paper's structure (Sec. 4): the same S(dt) built from
+ * cuFFT 2D transforms and separate elementwise kernels, several passes over
+ * psi per step.  Kept for timing and as a second witness; real time only,
+ * device psi only. */
+int spgpe_cufft_step_real(spgpe_ctx *ctx, void *psi, double dt, int nsteps);
+
+void spgpe_destroy(spgpe_ctx *ctx);
+const char *spgpe_last_error(const spgpe_ctx *ctx);
+int spgpe_version(void);
+
+/* Introspection for benchmarks: number of kernel launches the last step call
+ * issued (real time 2*nsteps + 1, imaginary time 3*nsteps + 1). */
+int spgpe_last_launches(const spgpe_ctx *ctx);
+
+/* Per-kernel timing for benchmarks.  While enabled (enable = 1), every fused
+ * launch is bracketed by CUDA events recorded on the context's stream.
+ * spgpe_timing synchronises and writes, for each kernel kind k in
+ * [0, SPGPE_NKINDS), the launch count count_out[k] and the summed event time
+ * ms_out[k] since timing was enabled, then restarts the accumulation.  Kinds:
+ * 0 real row pass opening, 1 real row pass fused (step end + next start),
+ * 2 real row pass closing, 3 real column pass, 4 imaginary row opening,
+ * 5 imaginary row pass B (scale + R + FFT), 6 imaginary row pass A (IFFT + R +
+ * norm partials), 7 imaginary rescale, 8 imaginary column pass. */
+#define SPGPE_NKINDS 9
+int spgpe_set_timing(spgpe_ctx *ctx, int enable);
+int spgpe_timing(spgpe_ctx *ctx, double *ms_out, int *count_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPGPE_H */

@@ -1,0 +1,239 @@
+"""GB300 (sm_103a) solver for the two-component quasi-2D GPE of arXiv:2010.15069.
+
+The hot path is the Strang time-splitting spectral step (Sec. 3.2, Eq. 13)
+run by hand-written CUDA kernels in ``libspgpe.so`` behind the C ABI of
+``include/spgpe.h``.  This package is the thin Python binding:
+
+* ``spgpe_*`` functions with the C names, taking raw pointers (``int``),
+  raising :class:`SpgpeError` on a negative status;
+* :class:`Context`, which takes torch CUDA tensors (device spinors, stepped
+  in place on the context's stream) or numpy arrays (host spinors, staged by
+  the library) and returns numpy results.
+
+PyTorch is used only for device memory and streams.  Nothing here computes
+any part of the method; importing works without the library, but every call
+needs it built (``paper_2010_15069_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SpgpeError,
+                   check, load)
+
+__all__ = [
+    "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SpgpeError",
+    "Context", "load",
+    "spgpe_init_grid", "spgpe_init_batch", "spgpe_set_potentials", "spgpe_set_potentials_separable",
+    "spgpe_step_real", "spgpe_step_imag", "spgpe_energy", "spgpe_norm", "spgpe_sync",
+    "spgpe_cufft_step_real", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
+    "spgpe_last_launches", "spgpe_set_timing", "spgpe_timing",
+]
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------ C-name layer
+
+def spgpe_init_grid(nx, ny, xmax, ymax, dtype=SPGPE_C64, stream=0):
+    ctx = ctypes.c_void_p()
+    check(load().spgpe_init_grid(ctypes.byref(ctx), int(nx), int(ny), float(xmax), float(ymax),
+                                 int(dtype), ctypes.c_void_p(int(stream))))
+    return ctx.value
+
+
+def spgpe_init_batch(nx, ny, xmax, ymax, ninst, dtype=SPGPE_C64, stream=0):
+    ctx = ctypes.c_void_p()
+    check(load().spgpe_init_batch(ctypes.byref(ctx), int(nx), int(ny), float(xmax), float(ymax),
+                                  int(ninst), int(dtype), ctypes.c_void_p(int(stream))))
+    return ctx.value
+
+
+def spgpe_set_potentials(ctx, V=None, delta=None, Omega=None, g11=0.0, g22=0.0, g12=0.0, kL=0.0):
+    V, delta, Omega = _f64(V), _f64(delta), _f64(Omega)
+    check(load().spgpe_set_potentials(ctx, _ptr(V), _ptr(delta), _ptr(Omega), float(g11), float(g22),
+                                      float(g12), float(kL)), ctx)
+
+
+def spgpe_set_potentials_separable(ctx, inst, Vx=None, Vy=None, delta_x=None, delta_y=None, Omega_x=None,
+                                   Omega_y=None, g11=0.0, g22=0.0, g12=0.0, kL=0.0):
+    arrs = [_f64(a) for a in (Vx, Vy, delta_x, delta_y, Omega_x, Omega_y)]
+    check(load().spgpe_set_potentials_separable(ctx, int(inst), *[_ptr(a) for a in arrs], float(g11),
+                                                float(g22), float(g12), float(kL)), ctx)
+
+
+def spgpe_step_real(ctx, psi_ptr, dt, nsteps):
+    check(load().spgpe_step_real(ctx, ctypes.c_void_p(int(psi_ptr)), float(dt), int(nsteps)), ctx)
+
+
+def spgpe_step_imag(ctx, psi_ptr, dtau, nsteps, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5),
+                    residual=False, ninst=1):
+    tgt = _f64(target, 2)
+    res = np.zeros(int(ninst)) if residual else None
+    check(load().spgpe_step_imag(ctx, ctypes.c_void_p(int(psi_ptr)), float(dtau), int(nsteps), int(norm_mode),
+                                 _ptr(tgt), _ptr(res)), ctx)
+    return res
+
+
+def spgpe_energy(ctx, psi_ptr, ninst=1):
+    out = np.zeros((int(ninst), 6))
+    check(load().spgpe_energy(ctx, ctypes.c_void_p(int(psi_ptr)), _ptr(out)), ctx)
+    return out
+
+
+def spgpe_norm(ctx, psi_ptr, ninst=1):
+    out = np.zeros((int(ninst), 2))
+    check(load().spgpe_norm(ctx, ctypes.c_void_p(int(psi_ptr)), _ptr(out)), ctx)
+    return out
+
+
+def spgpe_sync(ctx):
+    check(load().spgpe_sync(ctx), ctx)
+
+
+def spgpe_cufft_step_real(ctx, psi_ptr, dt, nsteps):
+    check(load().spgpe_cufft_step_real(ctx, ctypes.c_void_p(int(psi_ptr)), float(dt), int(nsteps)), ctx)
+
+
+def spgpe_destroy(ctx):
+    load().spgpe_destroy(ctx)
+
+
+def spgpe_last_error(ctx=None):
+    m = load().spgpe_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def spgpe_version():
+    return load().spgpe_version()
+
+
+def spgpe_last_launches(ctx):
+    return load().spgpe_last_launches(ctx)
+
+
+def spgpe_set_timing(ctx, enable):
+    check(load().spgpe_set_timing(ctx, int(bool(enable))), ctx)
+
+
+def spgpe_timing(ctx):
+    """{kind name: (launches, summed ms)} since timing was enabled (or last read)."""
+    from ._lib import KIND_NAMES, NKINDS
+    ms = np.zeros(NKINDS)
+    cnt = np.zeros(NKINDS, dtype=np.int32)
+    check(load().spgpe_timing(ctx, _ptr(ms), _ptr(cnt)), ctx)
+    return {KIND_NAMES[k]: (int(cnt[k]), float(ms[k])) for k in range(NKINDS) if cnt[k]}
+
+
+# --------------------------------------------------------- convenience class
+
+class Context:
+    """One solver context: an nx x ny grid (optionally a batch of instances).
+
+    Spinors are ``(2, ny, nx)`` or ``(ninst, 2, ny, nx)`` complex arrays:
+    torch CUDA tensors (complex64 for ``dtype="c64"``, complex128 for
+    ``"c128"``), stepped in place on this context's stream, or numpy arrays
+    on the host, which the library copies in, steps and copies back.
+    """
+
+    def __init__(self, nx, ny, xmax, ymax, dtype="c64", ninst=1, stream=None):
+        self.nx, self.ny, self.ninst = int(nx), int(ny), int(ninst)
+        self.dtype = {"c64": SPGPE_C64, "c128": SPGPE_C128}[dtype]
+        self.np_dtype = np.complex64 if self.dtype == SPGPE_C64 else np.complex128
+        self.stream = stream
+        s = 0
+        if stream is not None:
+            s = int(getattr(stream, "cuda_stream", stream))
+        self._ctx = (spgpe_init_batch(nx, ny, xmax, ymax, ninst, self.dtype, s) if ninst != 1
+                     else spgpe_init_grid(nx, ny, xmax, ymax, self.dtype, s))
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    def close(self):
+        if self._ctx:
+            spgpe_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check_psi(self, psi):
+        shape = tuple(psi.shape)
+        want = (2, self.ny, self.nx) if self.ninst == 1 else (self.ninst, 2, self.ny, self.nx)
+        if shape not in (want, (self.ninst, 2, self.ny, self.nx)):
+            raise ValueError(f"spinor shape {shape}, expected {want}")
+        if isinstance(psi, np.ndarray):
+            if psi.dtype != self.np_dtype or not psi.flags.c_contiguous:
+                raise ValueError(f"host spinor must be C-contiguous {np.dtype(self.np_dtype).name}")
+            return psi.ctypes.data
+        import torch  # device memory and streams only
+        want_t = torch.complex64 if self.dtype == SPGPE_C64 else torch.complex128
+        if psi.dtype != want_t or not psi.is_contiguous() or not psi.is_cuda:
+            raise ValueError(f"device spinor must be a contiguous CUDA {want_t} tensor")
+        return psi.data_ptr()
+
+    def set_potentials(self, V=None, delta=None, Omega=None, g11=0.0, g22=0.0, g12=0.0, kL=0.0):
+        n = self.nx * self.ny
+        spgpe_set_potentials(self._ctx, *(None if a is None else _f64(a, n) for a in (V, delta, Omega)),
+                             g11, g22, g12, kL)
+
+    def set_potentials_separable(self, inst=-1, Vx=None, Vy=None, delta_x=None, delta_y=None, Omega_x=None,
+                                 Omega_y=None, g11=0.0, g22=0.0, g12=0.0, kL=0.0):
+        nx, ny = self.nx, self.ny
+        spgpe_set_potentials_separable(self._ctx, inst, _f64(Vx, nx), _f64(Vy, ny), _f64(delta_x, nx),
+                                       _f64(delta_y, ny), _f64(Omega_x, nx), _f64(Omega_y, ny),
+                                       g11, g22, g12, kL)
+
+    def step_real(self, psi, dt, nsteps):
+        spgpe_step_real(self._ctx, self._check_psi(psi), dt, nsteps)
+        return psi
+
+    def step_imag(self, psi, dtau, nsteps, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5), residual=False):
+        return spgpe_step_imag(self._ctx, self._check_psi(psi), dtau, nsteps, norm_mode, target,
+                               residual, self.ninst)
+
+    def cufft_step_real(self, psi, dt, nsteps):
+        spgpe_cufft_step_real(self._ctx, self._check_psi(psi), dt, nsteps)
+        return psi
+
+    def energy(self, psi):
+        return spgpe_energy(self._ctx, self._check_psi(psi), self.ninst)
+
+    def norm(self, psi):
+        return spgpe_norm(self._ctx, self._check_psi(psi), self.ninst)
+
+    def sync(self):
+        spgpe_sync(self._ctx)
+
+    def last_launches(self):
+        return spgpe_last_launches(self._ctx)
+
+    def set_timing(self, enable=True):
+        spgpe_set_timing(self._ctx, enable)
+
+    def timing(self):
+        return spgpe_timing(self._ctx)

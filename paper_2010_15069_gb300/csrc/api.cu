@@ -1,0 +1,741 @@
+// C ABI of the fused TSSP solver (include/spgpe.h): context, operator tables,
+// step scheduling, reductions, and the cuFFT comparator.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/spgpe.h"
+#include "internal.h"
+
+using namespace spgpe;
+
+namespace {
+
+const double kTwoPi = 6.28318530717958647692528676655900577;
+
+thread_local std::string g_init_error;
+
+bool pow2_in_range(int n) { return n >= 8 && n <= 4096 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct spgpe_ctx {
+  int nx = 0, ny = 0, ninst = 1, dtype = 0;
+  double xmax = 0, ymax = 0, dx = 0, dy = 0;
+  cudaStream_t st = nullptr;
+  size_t es = 0;  // bytes per complex element
+
+  // Host FP64 model, per instance: x pieces [ninst][nx][3] = (V, delta, Omega),
+  // y pieces [ninst][ny][3], couplings [ninst][4] = (g11, g22, g12, kL).
+  std::vector<double> hx, hy, hg;
+  std::vector<char> inst_set;
+  bool has2d = false;
+
+  // Device tables.
+  void *d_twx = nullptr, *d_twy = nullptr;
+  void *d_tabx = nullptr, *d_taby = nullptr;  // step tables for (tab_dt, tab_imag)
+  void *d_rawx = nullptr, *d_rawy = nullptr;  // raw (V, delta, Omega) for energies
+  void *d_pot2d = nullptr;
+  void *d_kxt = nullptr, *d_kyt = nullptr;
+  double *d_gpar = nullptr;
+  double *d_partials = nullptr;
+  size_t n_partials = 0;
+  unsigned *d_counters = nullptr;
+  double *d_scale = nullptr;
+  int *d_flags = nullptr;
+  void *d_scratch = nullptr;  // psi-sized: energy transform / residual previous state
+  void *d_stage = nullptr;    // psi-sized: staging of host spinors
+  double tab_dt = NAN;
+  int tab_imag = -1;
+
+  cufftHandle plan = 0;
+  bool plan_ok = false;
+
+  std::string err;
+  int last_launches = 0;
+
+  // Optional per-launch timing (spgpe_set_timing): event pairs per kind.
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+
+  size_t psi_bytes() const { return (size_t)ninst * 2 * nx * ny * es; }
+  long plane() const { return (long)nx * ny; }
+};
+
+namespace {
+
+int fail(spgpe_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_init_error = msg;
+  return code;
+}
+
+int cuda_fail(spgpe_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, SPGPE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, expr)                                   \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr); \
+  } while (0)
+
+bool all_finite(const double *p, size_t n) {
+  if (!p) return true;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Upload FP64 values as the working precision T (float or double).
+int upload(spgpe_ctx *c, void *dst, const std::vector<double> &src) {
+  if (c->dtype == SPGPE_C64) {
+    std::vector<float> f(src.begin(), src.end());
+    CK(c, cudaMemcpyAsync(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
+  } else {
+    CK(c, cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  }
+  return SPGPE_OK;
+}
+
+int dev_alloc(spgpe_ctx *c, void **p, size_t bytes) {
+  if (*p) return SPGPE_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? SPGPE_ENOMEM : SPGPE_ECUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return SPGPE_OK;
+}
+
+void free_all(spgpe_ctx *c) {
+  for (auto &u : c->ev_used) {
+    cudaEventDestroy(u.second.first);
+    cudaEventDestroy(u.second.second);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  void *ps[] = {c->d_twx, c->d_twy, c->d_tabx, c->d_taby, c->d_rawx, c->d_rawy, c->d_pot2d, c->d_kxt,
+                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_flags, c->d_scratch,
+                c->d_stage};
+  for (void *p : ps)
+    if (p) cudaFree(p);
+  if (c->plan_ok) cufftDestroy(c->plan);
+}
+
+// Forward roots exp(-2 pi i m / n), FP64 then rounded once.
+std::vector<double> roots(int n) {
+  std::vector<double> w(2 * (size_t)n);
+  for (int m = 0; m < n; ++m) {
+    w[2 * m] = std::cos(kTwoPi * m / n);
+    w[2 * m + 1] = -std::sin(kTwoPi * m / n);
+  }
+  return w;
+}
+
+double kval(int i, int n, double d) { return kTwoPi * (i < n / 2 ? i : i - n) / (n * d); }
+
+// Raw (V, delta, Omega, 0) tables for the energy kernels.
+int upload_raw(spgpe_ctx *c) {
+  std::vector<double> rx((size_t)c->ninst * c->nx * 4), ry((size_t)c->ninst * c->ny * 4);
+  for (int i = 0; i < c->ninst; ++i) {
+    for (int x = 0; x < c->nx; ++x)
+      for (int k = 0; k < 3; ++k) rx[((size_t)i * c->nx + x) * 4 + k] = c->hx[((size_t)i * c->nx + x) * 3 + k];
+    for (int y = 0; y < c->ny; ++y)
+      for (int k = 0; k < 3; ++k) ry[((size_t)i * c->ny + y) * 4 + k] = c->hy[((size_t)i * c->ny + y) * 3 + k];
+  }
+  int r = upload(c, c->d_rawx, rx);
+  if (r) return r;
+  r = upload(c, c->d_rawy, ry);
+  if (r) return r;
+  CK(c, cudaMemcpyAsync(c->d_gpar, c->hg.data(), c->hg.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  c->tab_dt = NAN;  // step tables depend on the model
+  return SPGPE_OK;
+}
+
+// Step tables for substep dt (real or imaginary time):
+//   x/y step tables {V + delta/2, V - delta/2, c, s} of the separable pieces,
+//   (c, s) = (cos, sin) or (cosh, sinh) of Omega_piece * dt / 8 (X(dt/4));
+//   K tables a_j(kx) = exp(-i dt (kx^2/2 -+ kL kx)), b(ky) = exp(-i dt ky^2/2)/(nx ny)
+//   (imaginary time: the real exponentials exp(-dt (...))).
+int ensure_tables(spgpe_ctx *c, double dt, int imag) {
+  if (c->tab_dt == dt && c->tab_imag == imag) return SPGPE_OK;
+  const int nx = c->nx, ny = c->ny, ni = c->ninst;
+  std::vector<double> tx((size_t)ni * nx * 4), ty((size_t)ni * ny * 4);
+  auto rot = [&](double ang, double &cc, double &ss) {
+    if (imag) { cc = std::cosh(ang); ss = std::sinh(ang); }
+    else { cc = std::cos(ang); ss = std::sin(ang); }
+  };
+  for (int i = 0; i < ni; ++i) {
+    for (int x = 0; x < nx; ++x) {
+      const double *h = &c->hx[((size_t)i * nx + x) * 3];
+      double *o = &tx[((size_t)i * nx + x) * 4];
+      o[0] = h[0] + 0.5 * h[1];
+      o[1] = h[0] - 0.5 * h[1];
+      rot(h[2] * dt / 8.0, o[2], o[3]);
+    }
+    for (int y = 0; y < ny; ++y) {
+      const double *h = &c->hy[((size_t)i * ny + y) * 3];
+      double *o = &ty[((size_t)i * ny + y) * 4];
+      o[0] = h[0] + 0.5 * h[1];
+      o[1] = h[0] - 0.5 * h[1];
+      rot(h[2] * dt / 8.0, o[2], o[3]);
+    }
+  }
+  std::vector<double> kx((size_t)ni * 2 * nx * 2), ky((size_t)ny * 2);
+  const double inv = 1.0 / ((double)nx * ny);
+  for (int i = 0; i < ni; ++i) {
+    const double kL = c->hg[4 * i + 3];
+    for (int j = 0; j < 2; ++j)
+      for (int x = 0; x < nx; ++x) {
+        const double k = kval(x, nx, c->dx);
+        const double T = 0.5 * k * k + (j == 0 ? -kL : kL) * k;
+        double *o = &kx[(((size_t)i * 2 + j) * nx + x) * 2];
+        if (imag) { o[0] = std::exp(-dt * T); o[1] = 0.0; }
+        else { o[0] = std::cos(dt * T); o[1] = -std::sin(dt * T); }
+      }
+  }
+  for (int y = 0; y < ny; ++y) {
+    const double k = kval(y, ny, c->dy);
+    const double T = 0.5 * k * k;
+    if (imag) { ky[2 * y] = inv * std::exp(-dt * T); ky[2 * y + 1] = 0.0; }
+    else { ky[2 * y] = inv * std::cos(dt * T); ky[2 * y + 1] = -inv * std::sin(dt * T); }
+  }
+  int r;
+  if ((r = upload(c, c->d_tabx, tx)) || (r = upload(c, c->d_taby, ty)) || (r = upload(c, c->d_kxt, kx)) ||
+      (r = upload(c, c->d_kyt, ky)))
+    return r;
+  c->tab_dt = dt;
+  c->tab_imag = imag;
+  return SPGPE_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+RowArgs row_args(spgpe_ctx *c, void *psi, double dt) {
+  RowArgs a{};
+  a.psi = psi;
+  a.tabx = c->d_tabx;
+  a.taby = c->d_taby;
+  a.pot2d = c->has2d ? c->d_pot2d : nullptr;
+  a.tw = c->d_twx;
+  a.gpar = c->d_gpar;
+  a.tau = 0.5 * dt;
+  a.xang = dt / 8.0;
+  a.partials = c->d_partials;
+  a.counters = c->d_counters;
+  a.scale = c->d_scale;
+  a.tgt0 = 0.5;
+  a.tgt1 = 0.5;
+  a.norm_mode = 0;
+  a.wgt = c->dx * c->dy;
+  a.flags = c->d_flags;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.ninst = c->ninst;
+  return a;
+}
+
+ColArgs col_args(spgpe_ctx *c, void *psi) {
+  ColArgs a{};
+  a.psi = psi;
+  a.kxt = c->d_kxt;
+  a.kyt = c->d_kyt;
+  a.tw = c->d_twy;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.ninst = c->ninst;
+  return a;
+}
+
+cudaEvent_t take_event(spgpe_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int kind_of_row(int flags) {
+  switch (flags) {
+    case kRealFirst: return 0;
+    case kRealMid: return 1;
+    case kRealLast: return 2;
+    case kImagFirst: return 4;
+    case kImagB: return 5;
+    case kImagA: return 6;
+    default: return 7;
+  }
+}
+
+template <class F> cudaError_t timed(spgpe_ctx *c, int kind, F &&launch) {
+  ++c->last_launches;
+  if (!c->timing) return launch();
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(a, c->st);
+  if (e != cudaSuccess) return e;
+  e = launch();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(b, c->st);
+  c->ev_used.push_back({kind, {a, b}});
+  return e;
+}
+
+cudaError_t row(spgpe_ctx *c, int flags, const RowArgs &a) {
+  return timed(c, kind_of_row(flags), [&] {
+    return c->dtype == SPGPE_C64 ? launch_row<float>(flags, a, c->st) : launch_row<double>(flags, a, c->st);
+  });
+}
+
+cudaError_t col(spgpe_ctx *c, bool imag, const ColArgs &a) {
+  return timed(c, imag ? 8 : 3, [&] {
+    return c->dtype == SPGPE_C64 ? launch_col<float>(imag, a, c->st) : launch_col<double>(imag, a, c->st);
+  });
+}
+
+int check_ready(spgpe_ctx *c) {
+  if (!c) return SPGPE_EINVAL;
+  for (char s : c->inst_set)
+    if (!s) return fail(c, SPGPE_ESTATE, "potentials not set for every instance");
+  return SPGPE_OK;
+}
+
+// Resolve a caller spinor: device pointers are used in place, host spinors are
+// staged through the context's device buffer.
+int begin_psi(spgpe_ctx *c, const void *psi, void **dev, bool *host) {
+  *host = !is_device_ptr(psi);
+  if (!*host) {
+    *dev = const_cast<void *>(psi);
+    return SPGPE_OK;
+  }
+  int r = dev_alloc(c, &c->d_stage, c->psi_bytes());
+  if (r) return r;
+  CK(c, cudaMemcpyAsync(c->d_stage, psi, c->psi_bytes(), cudaMemcpyHostToDevice, c->st));
+  *dev = c->d_stage;
+  return SPGPE_OK;
+}
+
+int end_psi(spgpe_ctx *c, void *psi, bool host) {
+  if (!host) return SPGPE_OK;
+  CK(c, cudaMemcpyAsync(psi, c->d_stage, c->psi_bytes(), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return SPGPE_OK;
+}
+
+int read_flags(spgpe_ctx *c) {
+  int h = 0;
+  CK(c, cudaMemcpyAsync(&h, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  if (h) {
+    CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->st));
+    return fail(c, SPGPE_ENONFINITE, "non-finite or zero atom number met during imaginary-time renormalisation");
+  }
+  return SPGPE_OK;
+}
+
+int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int ninst, int dtype, void *stream) {
+  if (!out) return fail(nullptr, SPGPE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!pow2_in_range(nx) || !pow2_in_range(ny))
+    return fail(nullptr, SPGPE_EINVAL, "nx and ny must be powers of two in [8, 4096]");
+  if (!(std::isfinite(xmax) && xmax > 0 && std::isfinite(ymax) && ymax > 0))
+    return fail(nullptr, SPGPE_EINVAL, "xmax and ymax must be finite and positive");
+  if (dtype != SPGPE_C64 && dtype != SPGPE_C128) return fail(nullptr, SPGPE_EINVAL, "dtype must be SPGPE_C64 or SPGPE_C128");
+  if (ninst < 1 || ninst > 65535) return fail(nullptr, SPGPE_EINVAL, "ninst must be in [1, 65535]");
+  spgpe_ctx *c = new (std::nothrow) spgpe_ctx();
+  if (!c) return fail(nullptr, SPGPE_ENOMEM, "host allocation failed");
+  c->nx = nx;
+  c->ny = ny;
+  c->ninst = ninst;
+  c->dtype = dtype;
+  c->xmax = xmax;
+  c->ymax = ymax;
+  c->dx = 2.0 * xmax / nx;
+  c->dy = 2.0 * ymax / ny;
+  c->st = reinterpret_cast<cudaStream_t>(stream);
+  c->es = dtype == SPGPE_C64 ? 8 : 16;
+  c->hx.assign((size_t)ninst * nx * 3, 0.0);
+  c->hy.assign((size_t)ninst * ny * 3, 0.0);
+  c->hg.assign((size_t)ninst * 4, 0.0);
+  c->inst_set.assign(ninst, 0);
+  const size_t es = c->es, q = 2 * es;
+  // partial sums: row-pass renormalisation (ny blocks at most), energies
+  // (6 per row block + 2 per column block), norms (256 blocks of 2)
+  c->n_partials = (size_t)ninst * (6 * (size_t)ny + 2 * (size_t)nx + 2 * 1024);
+  int r;
+  if ((r = dev_alloc(c, &c->d_twx, nx * es)) || (r = dev_alloc(c, &c->d_twy, ny * es)) ||
+      (r = dev_alloc(c, &c->d_tabx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_taby, (size_t)ninst * ny * q)) ||
+      (r = dev_alloc(c, &c->d_rawx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_rawy, (size_t)ninst * ny * q)) ||
+      (r = dev_alloc(c, &c->d_kxt, (size_t)ninst * 2 * nx * es)) || (r = dev_alloc(c, &c->d_kyt, ny * es)) ||
+      (r = dev_alloc(c, (void **)&c->d_gpar, (size_t)ninst * 4 * sizeof(double))) ||
+      (r = dev_alloc(c, (void **)&c->d_partials, c->n_partials * sizeof(double))) ||
+      (r = dev_alloc(c, (void **)&c->d_counters, (size_t)ninst * sizeof(unsigned))) ||
+      (r = dev_alloc(c, (void **)&c->d_scale, (size_t)ninst * 2 * sizeof(double))) ||
+      (r = dev_alloc(c, (void **)&c->d_flags, sizeof(int)))) {
+    g_init_error = c->err;
+    free_all(c);
+    delete c;
+    return r;
+  }
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->d_counters, 0, (size_t)ninst * sizeof(unsigned), c->st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->st)) != cudaSuccess) {
+    g_init_error = cudaGetErrorString(e);
+    free_all(c);
+    delete c;
+    return SPGPE_ECUDA;
+  }
+  if ((r = upload(c, c->d_twx, roots(nx))) || (r = upload(c, c->d_twy, roots(ny)))) {
+    g_init_error = c->err;
+    free_all(c);
+    delete c;
+    return r;
+  }
+  *out = c;
+  return SPGPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spgpe_version(void) { return SPGPE_VERSION; }
+
+const char *spgpe_last_error(const spgpe_ctx *c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+int spgpe_last_launches(const spgpe_ctx *c) { return c ? c->last_launches : 0; }
+
+int spgpe_init_grid(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int dtype, void *stream) {
+  return init_common(out, nx, ny, xmax, ymax, 1, dtype, stream);
+}
+
+int spgpe_init_batch(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int ninst, int dtype,
+                     void *stream) {
+  return init_common(out, nx, ny, xmax, ymax, ninst, dtype, stream);
+}
+
+void spgpe_destroy(spgpe_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  free_all(c);
+  delete c;
+}
+
+int spgpe_set_potentials(spgpe_ctx *c, const double *V, const double *delta, const double *Omega, double g11,
+                         double g22, double g12, double kL) {
+  if (!c) return SPGPE_EINVAL;
+  const size_t n = (size_t)c->nx * c->ny;
+  if (!all_finite(V, n) || !all_finite(delta, n) || !all_finite(Omega, n))
+    return fail(c, SPGPE_EINVAL, "potential arrays must be finite");
+  const double g[4] = {g11, g22, g12, kL};
+  if (!all_finite(g, 4)) return fail(c, SPGPE_EINVAL, "couplings must be finite");
+  std::fill(c->hx.begin(), c->hx.end(), 0.0);
+  std::fill(c->hy.begin(), c->hy.end(), 0.0);
+  for (int i = 0; i < c->ninst; ++i)
+    for (int k = 0; k < 4; ++k) c->hg[4 * i + k] = g[k];
+  std::vector<double> p2(n * 4);
+  for (size_t i = 0; i < n; ++i) {
+    const double v = V ? V[i] : 0.0, d = delta ? delta[i] : 0.0, o = Omega ? Omega[i] : 0.0;
+    p2[4 * i] = v + 0.5 * d;
+    p2[4 * i + 1] = v - 0.5 * d;
+    p2[4 * i + 2] = o;
+    p2[4 * i + 3] = 0.0;
+  }
+  int r = dev_alloc(c, &c->d_pot2d, n * 2 * c->es);
+  if (r) return r;
+  if ((r = upload(c, c->d_pot2d, p2))) return r;
+  c->has2d = true;
+  if ((r = upload_raw(c))) return r;
+  CK(c, cudaStreamSynchronize(c->st));
+  std::fill(c->inst_set.begin(), c->inst_set.end(), 1);
+  return SPGPE_OK;
+}
+
+int spgpe_set_potentials_separable(spgpe_ctx *c, int inst, const double *Vx, const double *Vy, const double *delta_x,
+                                   const double *delta_y, const double *Omega_x, const double *Omega_y, double g11,
+                                   double g22, double g12, double kL) {
+  if (!c) return SPGPE_EINVAL;
+  if (inst < -1 || inst >= c->ninst) return fail(c, SPGPE_EINVAL, "instance index out of range");
+  const int nx = c->nx, ny = c->ny;
+  if (!all_finite(Vx, nx) || !all_finite(Vy, ny) || !all_finite(delta_x, nx) || !all_finite(delta_y, ny) ||
+      !all_finite(Omega_x, nx) || !all_finite(Omega_y, ny))
+    return fail(c, SPGPE_EINVAL, "potential pieces must be finite");
+  const double g[4] = {g11, g22, g12, kL};
+  if (!all_finite(g, 4)) return fail(c, SPGPE_EINVAL, "couplings must be finite");
+  if (c->has2d) {
+    // a separable call replaces the 2D model for every instance
+    c->has2d = false;
+    if (inst >= 0) std::fill(c->inst_set.begin(), c->inst_set.end(), 0);
+  }
+  const int i0 = inst < 0 ? 0 : inst, i1 = inst < 0 ? c->ninst : inst + 1;
+  for (int i = i0; i < i1; ++i) {
+    for (int x = 0; x < nx; ++x) {
+      double *h = &c->hx[((size_t)i * nx + x) * 3];
+      h[0] = Vx ? Vx[x] : 0.0;
+      h[1] = delta_x ? delta_x[x] : 0.0;
+      h[2] = Omega_x ? Omega_x[x] : 0.0;
+    }
+    for (int y = 0; y < ny; ++y) {
+      double *h = &c->hy[((size_t)i * ny + y) * 3];
+      h[0] = Vy ? Vy[y] : 0.0;
+      h[1] = delta_y ? delta_y[y] : 0.0;
+      h[2] = Omega_y ? Omega_y[y] : 0.0;
+    }
+    for (int k = 0; k < 4; ++k) c->hg[4 * i + k] = g[k];
+    c->inst_set[i] = 1;
+  }
+  int r = upload_raw(c);
+  if (r) return r;
+  CK(c, cudaStreamSynchronize(c->st));
+  return SPGPE_OK;
+}
+
+int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
+  int r = check_ready(c);
+  if (r) return r;
+  c->last_launches = 0;
+  if (!psi || nsteps < 0 || !std::isfinite(dt)) return fail(c, SPGPE_EINVAL, "bad psi, dt or nsteps");
+  if (nsteps == 0) return SPGPE_OK;
+  if ((r = ensure_tables(c, dt, 0))) return r;
+  void *p;
+  bool host;
+  if ((r = begin_psi(c, psi, &p, &host))) return r;
+  const RowArgs ra = row_args(c, p, dt);
+  const ColArgs ca = col_args(c, p);
+  CK(c, row(c, kRealFirst, ra));
+  for (int s = 1; s <= nsteps; ++s) {
+    CK(c, col(c, false, ca));
+    CK(c, row(c, s < nsteps ? kRealMid : kRealLast, ra));
+  }
+  return end_psi(c, psi, host);
+}
+
+int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_mode, const double *target,
+                    double *residual_out) {
+  int r = check_ready(c);
+  if (r) return r;
+  c->last_launches = 0;
+  if (!psi || nsteps < 0 || !std::isfinite(dtau)) return fail(c, SPGPE_EINVAL, "bad psi, dtau or nsteps");
+  if (norm_mode != SPGPE_NORM_TOTAL && norm_mode != SPGPE_NORM_PER_COMPONENT)
+    return fail(c, SPGPE_EINVAL, "bad norm_mode");
+  const double t0 = target ? target[0] : 0.5, t1 = target ? target[1] : 0.5;
+  if (!(std::isfinite(t0) && std::isfinite(t1) && t0 >= 0 && t1 >= 0 && t0 + t1 > 0))
+    return fail(c, SPGPE_EINVAL, "targets must be finite, non-negative, not both zero");
+  if (nsteps == 0) {
+    if (residual_out)
+      for (int i = 0; i < c->ninst; ++i) residual_out[i] = NAN;
+    return SPGPE_OK;
+  }
+  if ((r = ensure_tables(c, dtau, 1))) return r;
+  if (residual_out && (r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
+  void *p;
+  bool host;
+  if ((r = begin_psi(c, psi, &p, &host))) return r;
+  RowArgs ra = row_args(c, p, dtau);
+  ra.tgt0 = t0;
+  ra.tgt1 = t1;
+  ra.norm_mode = norm_mode;
+  const ColArgs ca = col_args(c, p);
+  for (int s = 1; s <= nsteps; ++s) {
+    if (s == nsteps && residual_out) {
+      // Keep Psi_n (normalised) for the residual of the last step.
+      if (s > 1) CK(c, row(c, kImagScale, ra));
+      CK(c, cudaMemcpyAsync(c->d_scratch, p, c->psi_bytes(), cudaMemcpyDeviceToDevice, c->st));
+      CK(c, row(c, kImagFirst, ra));
+    } else {
+      CK(c, row(c, s == 1 ? kImagFirst : kImagB, ra));
+    }
+    CK(c, col(c, true, ca));
+    CK(c, row(c, kImagA, ra));
+  }
+  CK(c, row(c, kImagScale, ra));
+  if (residual_out) {
+    const int blocks = 128;
+    ++c->last_launches;
+    if (c->dtype == SPGPE_C64)
+      CK(c, launch_residual<float>(p, c->d_scratch, c->plane(), c->ninst, c->d_partials, blocks, c->st));
+    else
+      CK(c, launch_residual<double>(p, c->d_scratch, c->plane(), c->ninst, c->d_partials, blocks, c->st));
+    std::vector<double> h((size_t)c->ninst * blocks * 2);
+    CK(c, cudaMemcpyAsync(h.data(), c->d_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    for (int i = 0; i < c->ninst; ++i) {
+      double num = 0, den = 0;
+      for (int b = 0; b < blocks; ++b) {
+        num += h[((size_t)i * blocks + b) * 2];
+        den += h[((size_t)i * blocks + b) * 2 + 1];
+      }
+      residual_out[i] = std::sqrt(num / den) / dtau;
+    }
+  }
+  if ((r = end_psi(c, psi, host))) return r;
+  if (residual_out || host) return read_flags(c);
+  return SPGPE_OK;
+}
+
+int spgpe_set_timing(spgpe_ctx *c, int enable) {
+  if (!c) return SPGPE_EINVAL;
+  c->timing = enable != 0;
+  return SPGPE_OK;
+}
+
+int spgpe_timing(spgpe_ctx *c, double *ms_out, int *count_out) {
+  if (!c || !ms_out || !count_out) return SPGPE_EINVAL;
+  CK(c, cudaStreamSynchronize(c->st));
+  for (int k = 0; k < SPGPE_NKINDS; ++k) {
+    ms_out[k] = 0.0;
+    count_out[k] = 0;
+  }
+  for (auto &u : c->ev_used) {
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, u.second.first, u.second.second));
+    ms_out[u.first] += ms;
+    count_out[u.first] += 1;
+    c->ev_pool.push_back(u.second.first);
+    c->ev_pool.push_back(u.second.second);
+  }
+  c->ev_used.clear();
+  return SPGPE_OK;
+}
+
+int spgpe_sync(spgpe_ctx *c) {
+  if (!c) return SPGPE_EINVAL;
+  CK(c, cudaStreamSynchronize(c->st));
+  return read_flags(c);
+}
+
+int spgpe_norm(spgpe_ctx *c, const void *psi, double *out) {
+  if (!c || !psi || !out) return fail(c, SPGPE_EINVAL, "NULL argument");
+  void *p;
+  bool host;
+  int r = begin_psi(c, psi, &p, &host);
+  if (r) return r;
+  const int blocks = 128;
+  if (c->dtype == SPGPE_C64) CK(c, launch_norm<float>(p, c->plane(), c->ninst, c->d_partials, blocks, c->st));
+  else CK(c, launch_norm<double>(p, c->plane(), c->ninst, c->d_partials, blocks, c->st));
+  std::vector<double> h((size_t)c->ninst * blocks * 2);
+  CK(c, cudaMemcpyAsync(h.data(), c->d_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  bool finite = true;
+  for (int i = 0; i < c->ninst; ++i) {
+    double su = 0, sd = 0;
+    for (int b = 0; b < blocks; ++b) {
+      su += h[((size_t)i * blocks + b) * 2];
+      sd += h[((size_t)i * blocks + b) * 2 + 1];
+    }
+    out[2 * i] = su * c->dx * c->dy;
+    out[2 * i + 1] = sd * c->dx * c->dy;
+    finite = finite && std::isfinite(out[2 * i]) && std::isfinite(out[2 * i + 1]);
+  }
+  return finite ? SPGPE_OK : fail(c, SPGPE_ENONFINITE, "non-finite atom number");
+}
+
+int spgpe_energy(spgpe_ctx *c, const void *psi, double *out) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!psi || !out) return fail(c, SPGPE_EINVAL, "NULL argument");
+  if ((r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
+  void *p;
+  bool host;
+  if ((r = begin_psi(c, psi, &p, &host))) return r;
+  EnergyArgs a{};
+  a.psi = p;
+  a.scratch = c->d_scratch;
+  a.rawx = c->d_rawx;
+  a.rawy = c->d_rawy;
+  a.pot2d = c->has2d ? c->d_pot2d : nullptr;
+  a.twx = c->d_twx;
+  a.twy = c->d_twy;
+  a.gpar = c->d_gpar;
+  a.partials = c->d_partials;
+  a.dkx = kTwoPi / (c->nx * c->dx);
+  a.dky = kTwoPi / (c->ny * c->dy);
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.ninst = c->ninst;
+  int rb = 0, cb = 0;
+  if (c->dtype == SPGPE_C64) CK(c, launch_energy<float>(a, c->st, &rb, &cb));
+  else CK(c, launch_energy<double>(a, c->st, &rb, &cb));
+  const size_t nrow = (size_t)c->ninst * rb * 6, ncol = (size_t)c->ninst * 2 * cb;
+  std::vector<double> h(nrow + ncol);
+  CK(c, cudaMemcpyAsync(h.data(), c->d_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  const double w = c->dx * c->dy;
+  bool finite = true;
+  for (int i = 0; i < c->ninst; ++i) {
+    double s[6] = {0, 0, 0, 0, 0, 0}, kin = 0;
+    for (int b = 0; b < rb; ++b)
+      for (int k = 0; k < 6; ++k) s[k] += h[((size_t)i * rb + b) * 6 + k];
+    for (int j = 0; j < 2; ++j)
+      for (int b = 0; b < cb; ++b) kin += h[nrow + ((size_t)i * 2 + j) * cb + b];
+    double *o = out + 6 * (size_t)i;
+    o[1] = kin * w / ((double)c->nx * c->ny);
+    o[2] = s[0] * w;
+    o[3] = s[1] * w;
+    o[4] = s[2] * w;
+    o[5] = s[3] * w;
+    o[0] = o[1] + o[2] + o[3] + o[4] + o[5];
+    for (int k = 0; k < 6; ++k) finite = finite && std::isfinite(o[k]);
+  }
+  return finite ? SPGPE_OK : fail(c, SPGPE_ENONFINITE, "non-finite energy");
+}
+
+int spgpe_cufft_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
+  int r = check_ready(c);
+  if (r) return r;
+  c->last_launches = 0;
+  if (!psi || nsteps < 0 || !std::isfinite(dt)) return fail(c, SPGPE_EINVAL, "bad psi, dt or nsteps");
+  if (!is_device_ptr(psi)) return fail(c, SPGPE_EINVAL, "the comparator takes device spinors only");
+  if (nsteps == 0) return SPGPE_OK;
+  if ((r = ensure_tables(c, dt, 0))) return r;
+  if (!c->plan_ok) {
+    int n[2] = {c->ny, c->nx};
+    const cufftType ty = c->dtype == SPGPE_C64 ? CUFFT_C2C : CUFFT_Z2Z;
+    if (cufftPlanMany(&c->plan, 2, n, nullptr, 1, 0, nullptr, 1, 0, ty, 2 * c->ninst) != CUFFT_SUCCESS)
+      return fail(c, SPGPE_ECUDA, "cufftPlanMany failed");
+    c->plan_ok = true;
+  }
+  if (cufftSetStream(c->plan, c->st) != CUFFT_SUCCESS) return fail(c, SPGPE_ECUDA, "cufftSetStream failed");
+  const RowArgs ra = row_args(c, psi, dt);
+  const ColArgs ca = col_args(c, psi);
+  for (int s = 0; s < nsteps; ++s) {
+    if (c->dtype == SPGPE_C64) {
+      CK(c, launch_ref_R<float>(false, ra, c->st));
+      if (cufftExecC2C(c->plan, (cufftComplex *)psi, (cufftComplex *)psi, CUFFT_FORWARD) != CUFFT_SUCCESS)
+        return fail(c, SPGPE_ECUDA, "cufftExecC2C failed");
+      CK(c, launch_ref_K<float>(ca, c->st));
+      if (cufftExecC2C(c->plan, (cufftComplex *)psi, (cufftComplex *)psi, CUFFT_INVERSE) != CUFFT_SUCCESS)
+        return fail(c, SPGPE_ECUDA, "cufftExecC2C failed");
+      CK(c, launch_ref_R<float>(false, ra, c->st));
+    } else {
+      CK(c, launch_ref_R<double>(false, ra, c->st));
+      if (cufftExecZ2Z(c->plan, (cufftDoubleComplex *)psi, (cufftDoubleComplex *)psi, CUFFT_FORWARD) != CUFFT_SUCCESS)
+        return fail(c, SPGPE_ECUDA, "cufftExecZ2Z failed");
+      CK(c, launch_ref_K<double>(ca, c->st));
+      if (cufftExecZ2Z(c->plan, (cufftDoubleComplex *)psi, (cufftDoubleComplex *)psi, CUFFT_INVERSE) != CUFFT_SUCCESS)
+        return fail(c, SPGPE_ECUDA, "cufftExecZ2Z failed");
+      CK(c, launch_ref_R<double>(false, ra, c->st));
+    }
+    c->last_launches += 3;
+  }
+  return SPGPE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Declarations shared by the kernel translation units and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace spgpe {
+
+// Row-pass work flags (one fused launch does the listed steps in order).
+enum : int {
+  F_IFFT = 1,     // load k_x-space row, inverse FFT along x
+  F_REND = 2,     // R(dt/2) = X(dt/4) D(dt/2) X(dt/4): the step's closing half
+  F_PART = 4,     // FP64 atom-number partials of the result; last block -> scale
+  F_SCALE = 8,    // multiply by the per-instance scale (imaginary-time renormalisation)
+  F_RSTART = 16,  // R(dt/2): the next step's opening half
+  F_FFT = 32,     // forward FFT along x, store k_x-space row
+  F_IMAG = 64     // imaginary time: exp(-tau H) factors instead of exp(-i tau H)
+};
+
+constexpr int kRealFirst = F_RSTART | F_FFT;
+constexpr int kRealMid = F_IFFT | F_REND | F_RSTART | F_FFT;
+constexpr int kRealLast = F_IFFT | F_REND;
+constexpr int kImagFirst = F_IMAG | F_RSTART | F_FFT;
+constexpr int kImagB = F_IMAG | F_SCALE | F_RSTART | F_FFT;
+constexpr int kImagA = F_IMAG | F_IFFT | F_REND | F_PART;
+constexpr int kImagScale = F_IMAG | F_SCALE;
+
+// Arguments of the fused row pass (x direction, both components per thread).
+struct RowArgs {
+  void *psi;              // [ninst][2][ny][nx] complex, in place
+  const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, c, s} step table
+  const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, c, s} step table
+  const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
+  const void *tw;         // [nx] forward roots exp(-2 pi i m / nx)
+  const double *gpar;     // [ninst][4] {g11, g22, g12, kL}
+  double tau;             // D substep (dt/2)
+  double xang;            // X(dt/4) rotation angle per unit Omega (dt/8)
+  double *partials;       // [ninst][gridDim.x][2]
+  unsigned *counters;     // [ninst], zero between launches
+  double *scale;          // [ninst][2]
+  double tgt0, tgt1;      // target atom numbers
+  int norm_mode;          // 0 total, 1 per component
+  double wgt;             // dx * dy
+  int *flags;             // bit 0: non-finite or zero norm met
+  int nx, ny, ninst, rows;
+};
+
+// Arguments of the fused column pass (y direction, one component per block).
+struct ColArgs {
+  void *psi;
+  const void *kxt;        // [ninst][2][nx] complex factor a_j(kx)
+  const void *kyt;        // [ny] complex factor b(ky), includes 1/(nx ny)
+  const void *tw;         // [ny] forward roots
+  int nx, ny, ninst, C;
+};
+
+// Energy passes.
+struct EnergyArgs {
+  const void *psi;
+  void *scratch;          // [ninst][2][ny][nx] k_x-space copy
+  const void *rawx;       // [ninst][nx] {Vx, delta_x, Omega_x, 0}
+  const void *rawy;       // [ninst][ny] {Vy, delta_y, Omega_y, 0}
+  const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
+  const void *twx, *twy;
+  const double *gpar;
+  double *partials;       // row pass: [ninst][gridDim.x][6]; column pass: [ninst][2][gridDim.x]
+  double dkx, dky;        // 2 pi / (n d)
+  int nx, ny, ninst, rows, C;
+};
+
+constexpr int kRowMaxThreads = 256;
+constexpr int kColMaxThreads = 512;
+
+// Shared-memory element counts (host and device use the same formulas).
+// One padding slot per 128-byte line keeps strided Stockham writes free of
+// bank conflicts.
+__host__ __device__ constexpr int pad_shift(int elem_bytes) { return elem_bytes == 8 ? 4 : 3; }
+__host__ __device__ constexpr int row_pad_n(int n, int elem_bytes) { return n + (n >> pad_shift(elem_bytes)); }
+__host__ __device__ constexpr int row_stride(int n, int elem_bytes) { return 2 * row_pad_n(n, elem_bytes) + 2; }
+__host__ __device__ constexpr int col_smem_elems(int n, int c, int elem_bytes) {
+  return n * c + ((n * c) >> pad_shift(elem_bytes)) + 1;
+}
+
+// Launch geometry of the fused passes (host and device agree on it).
+struct LaunchShape {
+  int elems_per_thread;   // E: elements of one sequence held per thread
+  int threads;            // block size
+  int blocks_x;           // blocks per instance (row groups or column groups)
+  int rows_or_cols;       // rows per block (row pass) or columns per block (column pass)
+  size_t smem;            // dynamic shared memory bytes
+};
+
+// Per-precision launchers (T = float for SPGPE_C64, double for SPGPE_C128),
+// explicitly instantiated in kernels_row.cu and kernels_col.cu.  They return
+// cudaGetLastError() after the launch.
+template <class T> LaunchShape row_shape(int nx, int ny);
+template <class T> LaunchShape col_shape(int nx, int ny);
+template <class T> cudaError_t launch_row(int flags, RowArgs a, cudaStream_t s);
+template <class T> cudaError_t launch_col(bool imag, ColArgs a, cudaStream_t s);
+template <class T> cudaError_t launch_energy(EnergyArgs a, cudaStream_t s, int *row_blocks, int *col_blocks);
+template <class T> cudaError_t launch_norm(const void *psi, long plane, int ninst, double *partials, int blocks,
+                                           cudaStream_t s);
+template <class T> cudaError_t launch_residual(const void *psi, const void *prev, long plane, int ninst,
+                                               double *partials, int blocks, cudaStream_t s);
+template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStream_t s);
+template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t s);
+
+}  // namespace spgpe

@@ -1,0 +1,468 @@
+// Fused TSSP passes for the two-component GPE (templates; instantiated per
+// precision in kernels_row.cu / kernels_col.cu).
+//
+// One step S(dt) = R(dt/2) F^-1 K(dt) F R(dt/2) (Sec. 3.2, Eq. 13) is run as
+//   row pass    : [inverse x-FFT] -> R(dt/2) [-> R(dt/2) of the next step] -> x-FFT
+//   column pass : y-FFT -> K(dt) -> inverse y-FFT
+// so psi crosses HBM twice per real-time step.  The row pass holds both
+// components of a row in registers (R mixes them through X = exp(-i tau
+// Omega sigma_x / 2) and the g12 density); the column pass holds one
+// component of C adjacent columns (K is diagonal in spin).  Imaginary time
+// splits the row pass at the renormalisation point: pass A ends the step and
+// produces FP64 atom-number partials, the last block of each instance turns
+// them into the scale, and pass B applies it before the next R(dt/2).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace spgpe {
+
+template <class T>
+struct alignas(4 * sizeof(T)) q4 {
+  T x, y, z, w;
+};
+
+// ------------------------------------------------------------ math helpers
+
+template <class T> __device__ __forceinline__ T d_exp(T a) {
+  if constexpr (std::is_same<T, float>::value) return expf(a); else return exp(a);
+}
+template <class T> __device__ __forceinline__ void d_sincos(T a, T *s, T *c) {
+  if constexpr (std::is_same<T, float>::value) sincosf(a, s, c); else sincos(a, s, c);
+}
+template <class T> __device__ __forceinline__ T d_cosh(T a) {
+  if constexpr (std::is_same<T, float>::value) return coshf(a); else return cosh(a);
+}
+template <class T> __device__ __forceinline__ T d_sinh(T a) {
+  if constexpr (std::is_same<T, float>::value) return sinhf(a); else return sinh(a);
+}
+
+// Rotation coefficients of X for an angle: (cos, sin) in real time, (cosh,
+// sinh) in imaginary time; compose() adds two angles.
+template <bool IMAG, class T> __device__ __forceinline__ void rot_of(T ang, T &c, T &s) {
+  if constexpr (IMAG) { c = d_cosh(ang); s = d_sinh(ang); } else { d_sincos(ang, &s, &c); }
+}
+template <bool IMAG, class T> __device__ __forceinline__ void rot_compose(T &c, T &s, T c2, T s2) {
+  const T nc = IMAG ? c * c2 + s * s2 : c * c2 - s * s2;
+  const T ns = s * c2 + c * s2;
+  c = nc;
+  s = ns;
+}
+
+// X: (u, d) <- exp(-i theta sigma_x) (u, d), theta the half-angle whose
+// (cos, sin) are (c, s); imaginary time exp(-theta sigma_x) with (cosh, sinh).
+template <bool IMAG, class T> __device__ __forceinline__ void opX(cx<T> &u, cx<T> &d, T c, T s) {
+  const cx<T> a = u, b = d;
+  if constexpr (IMAG) {
+    u = {c * a.re - s * b.re, c * a.im - s * b.im};
+    d = {c * b.re - s * a.re, c * b.im - s * a.im};
+  } else {
+    u = {c * a.re + s * b.im, c * a.im - s * b.re};
+    d = {c * b.re + s * a.im, c * b.im - s * a.re};
+  }
+}
+
+// D(tau): diagonal potential + mean-field phase (decay), densities on entry.
+template <bool IMAG, class T>
+__device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T tau) {
+  const T ru = cabs2(u), rd = cabs2(d);
+  const T eu = vu + g11 * ru + g12 * rd;
+  const T ed = vd + g22 * rd + g12 * ru;
+  if constexpr (IMAG) {
+    u = cscale(u, d_exp(-tau * eu));
+    d = cscale(d, d_exp(-tau * ed));
+  } else {
+    T su, cu, sd, cd;
+    d_sincos(-tau * eu, &su, &cu);
+    d_sincos(-tau * ed, &sd, &cd);
+    u = cmul(u, cx<T>{cu, su});
+    d = cmul(d, cx<T>{cd, sd});
+  }
+}
+
+// --------------------------------------------------------- block reductions
+
+// Deterministic block sum of K doubles (fixed shuffle tree, fixed warp order).
+// Every thread must call it; the result is valid in thread 0.
+template <int K> __device__ __forceinline__ void block_sum(double (&v)[K]) {
+  __shared__ double red[K][32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k][w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = (l < nw) ? red[k][l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------- shared-memory layouts
+
+template <class T> struct RowAcc {
+  static constexpr int SH = pad_shift(sizeof(cx<T>));
+  cx<T> *base;
+  int stride;
+  __device__ __forceinline__ void st(int q, int p, cx<T> v) const { base[q * stride + p + (p >> SH)] = v; }
+  __device__ __forceinline__ cx<T> ld(int q, int p) const { return base[q * stride + p + (p >> SH)]; }
+};
+
+template <class T> struct ColAcc {
+  static constexpr int SH = pad_shift(sizeof(cx<T>));
+  cx<T> *base;
+  int C, c;
+  __device__ __forceinline__ int idx(int p) const { const int e = p * C + c; return e + (e >> SH); }
+  __device__ __forceinline__ void st(int, int p, cx<T> v) const { base[idx(p)] = v; }
+  __device__ __forceinline__ cx<T> ld(int, int p) const { return base[idx(p)]; }
+};
+
+// ------------------------------------------------------------- row pass
+
+template <class T, int LOGN, int LOGE, int F>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxThreads) row_pass(const RowArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+  constexpr bool IMAG = (F & F_IMAG) != 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+  const int lrow = threadIdx.x / TT, t = threadIdx.x - lrow * TT;
+  const int inst = blockIdx.y;
+  const int y = blockIdx.x * a.rows + lrow;
+  const long plane = (long)a.ny * N;
+  cx<T> *up = reinterpret_cast<cx<T> *>(a.psi) + (long)inst * 2 * plane + (long)y * N;
+  cx<T> *dn = up + plane;
+  const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+  const RowAcc<T> acc{sm + lrow * row_stride(N, sizeof(cx<T>)), row_pad_n(N, sizeof(cx<T>))};
+
+  cx<T> v[2][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    v[0][m] = up[t + m * TT];
+    v[1][m] = dn[t + m * TT];
+  }
+  if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 2>(v, t, tw, acc);
+
+  double nsum[2] = {0.0, 0.0};
+  if constexpr (F & (F_REND | F_RSTART | F_SCALE)) {
+    T sc0 = T(1), sc1 = T(1);
+    if constexpr (F & F_SCALE) {
+      sc0 = T(a.scale[2 * inst]);
+      sc1 = T(a.scale[2 * inst + 1]);
+    }
+    const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
+    const q4<T> *tx = reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
+    const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
+    const T g11 = T(a.gpar[4 * inst]), g22 = T(a.gpar[4 * inst + 1]), g12 = T(a.gpar[4 * inst + 2]);
+    const T tau = T(a.tau), xang = T(a.xang);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int x = t + m * TT;
+      cx<T> &u = v[0][m];
+      cx<T> &d = v[1][m];
+      if constexpr (F & F_SCALE) {
+        u = cscale(u, sc0);
+        d = cscale(d, sc1);
+      }
+      if constexpr (F & (F_REND | F_RSTART)) {
+        const q4<T> px = tx[x];
+        T vu = px.x + ty.x, vd = px.y + ty.y;
+        T c = px.z, s = px.w;
+        rot_compose<IMAG>(c, s, ty.z, ty.w);
+        if (p2) {
+          const q4<T> q = p2[(long)y * N + x];
+          vu += q.x;
+          vd += q.y;
+          T c2, s2;
+          rot_of<IMAG>(q.z * xang, c2, s2);
+          rot_compose<IMAG>(c, s, c2, s2);
+        }
+        if constexpr (F & F_REND) {
+          opX<IMAG>(u, d, c, s);
+          opD<IMAG>(u, d, vu, vd, g11, g22, g12, tau);
+          opX<IMAG>(u, d, c, s);
+        }
+        if constexpr (F & F_PART) {
+          nsum[0] += double(cabs2(u));
+          nsum[1] += double(cabs2(d));
+        }
+        if constexpr (F & F_RSTART) {
+          opX<IMAG>(u, d, c, s);
+          opD<IMAG>(u, d, vu, vd, g11, g22, g12, tau);
+          opX<IMAG>(u, d, c, s);
+        }
+      }
+    }
+  }
+
+  if constexpr (F & F_PART) {
+    // FP64 atom-number partials; the last block of this instance reduces them
+    // in a fixed order and writes the renormalisation scale (Sec. 3.2).
+    __shared__ int s_last;
+    block_sum<2>(nsum);
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+      a.partials[((long)inst * G + blockIdx.x) * 2] = nsum[0];
+      a.partials[((long)inst * G + blockIdx.x) * 2 + 1] = nsum[1];
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.counters[inst], 1u);
+      s_last = (prev == (unsigned)G - 1u);
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double tot[2] = {0.0, 0.0};
+      for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        tot[0] += __ldcg(&a.partials[((long)inst * G + b) * 2]);
+        tot[1] += __ldcg(&a.partials[((long)inst * G + b) * 2 + 1]);
+      }
+      block_sum<2>(tot);
+      if (threadIdx.x == 0) {
+        const double nu = tot[0] * a.wgt, nd = tot[1] * a.wgt;
+        double s0, s1;
+        if (a.norm_mode == 1) {
+          s0 = sqrt(a.tgt0 / nu);
+          s1 = sqrt(a.tgt1 / nd);
+        } else {
+          s0 = s1 = sqrt((a.tgt0 + a.tgt1) / (nu + nd));
+        }
+        if (!isfinite(s0) || !isfinite(s1)) atomicOr(a.flags, 1);
+        a.scale[2 * inst] = s0;
+        a.scale[2 * inst + 1] = s1;
+        a.counters[inst] = 0u;
+      }
+    }
+  }
+
+  if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 2>(v, t, tw, acc);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    up[t + m * TT] = v[0][m];
+    dn[t + m * TT] = v[1][m];
+  }
+}
+
+// ---------------------------------------------------------- column pass
+
+template <class T, int LOGN, int LOGE, bool IMAG>
+__global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = a.C;
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  const int comp = blockIdx.y, inst = blockIdx.z;
+  const int kx = blockIdx.x * C + c;
+  cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + ((long)inst * 2 + comp) * (long)N * a.nx + kx;
+  const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+  const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
+
+  cx<T> v[1][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[0][m] = col[(long)(t + m * TT) * a.nx];
+  block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);
+  const cx<T> ax = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
+  const cx<T> *by = reinterpret_cast<const cx<T> *>(a.kyt);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const cx<T> b = by[t + m * TT];
+    if constexpr (IMAG) {
+      v[0][m] = cscale(v[0][m], ax.re * b.re);
+    } else {
+      v[0][m] = cmul(v[0][m], cmul(ax, b));
+    }
+  }
+  block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
+#pragma unroll
+  for (int m = 0; m < E; ++m) col[(long)(t + m * TT) * a.nx] = v[0][m];
+}
+
+// --------------------------------------------------------- energy passes
+
+__device__ __forceinline__ int kbin(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// Real-space energy densities (trap, detuning, Raman, interaction, atom
+// numbers) in FP64, then the forward x-FFT of both components into scratch.
+template <class T, int LOGN, int LOGE>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxThreads) energy_row(const EnergyArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+  const int lrow = threadIdx.x / TT, t = threadIdx.x - lrow * TT;
+  const int inst = blockIdx.y;
+  const int y = blockIdx.x * a.rows + lrow;
+  const long plane = (long)a.ny * N;
+  const long off = (long)inst * 2 * plane + (long)y * N;
+  const cx<T> *up = reinterpret_cast<const cx<T> *>(a.psi) + off;
+  const cx<T> *dn = up + plane;
+  cx<T> *oup = reinterpret_cast<cx<T> *>(a.scratch) + off;
+  cx<T> *odn = oup + plane;
+  const RowAcc<T> acc{sm + lrow * row_stride(N, sizeof(cx<T>)), row_pad_n(N, sizeof(cx<T>))};
+  const q4<T> ry = reinterpret_cast<const q4<T> *>(a.rawy)[(long)inst * a.ny + y];
+  const q4<T> *rx = reinterpret_cast<const q4<T> *>(a.rawx) + (long)inst * N;
+  const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
+  const double g11 = a.gpar[4 * inst], g22 = a.gpar[4 * inst + 1], g12 = a.gpar[4 * inst + 2];
+
+  cx<T> v[2][E];
+  double acc6[6] = {0, 0, 0, 0, 0, 0};  // trap, detuning, Raman, interaction, N_up, N_dn
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int x = t + m * TT;
+    v[0][m] = up[x];
+    v[1][m] = dn[x];
+    const q4<T> px = rx[x];
+    double V = double(px.x) + double(ry.x), de = double(px.y) + double(ry.y), Om = double(px.z) + double(ry.z);
+    if (p2) {
+      const q4<T> q = p2[(long)y * N + x];
+      V += 0.5 * (double(q.x) + double(q.y));
+      de += double(q.x) - double(q.y);
+      Om += double(q.z);
+    }
+    const double ur = v[0][m].re, ui = v[0][m].im, dr = v[1][m].re, di = v[1][m].im;
+    const double ru = ur * ur + ui * ui, rd = dr * dr + di * di;
+    acc6[0] += V * (ru + rd);
+    acc6[1] += 0.5 * de * (ru - rd);
+    acc6[2] += Om * (ur * dr + ui * di);
+    acc6[3] += 0.5 * g11 * ru * ru + 0.5 * g22 * rd * rd + g12 * ru * rd;
+    acc6[4] += ru;
+    acc6[5] += rd;
+  }
+  block_sum<6>(acc6);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.partials[((long)inst * gridDim.x + blockIdx.x) * 6 + k] = acc6[k];
+  block_fft<LOGN, LOGE, -1, 2>(v, t, reinterpret_cast<const cx<T> *>(a.twx), acc);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    oup[t + m * TT] = v[0][m];
+    odn[t + m * TT] = v[1][m];
+  }
+}
+
+// Forward y-FFT of the scratch columns and the kinetic sum
+// sum_k T_j(k) |psi_hat_j(k)|^2 with T_j = k^2/2 -+ kL kx, in FP64.
+template <class T, int LOGN, int LOGE>
+__global__ void __launch_bounds__(512) energy_col(const EnergyArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = a.C;
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  const int comp = blockIdx.y, inst = blockIdx.z;
+  const int ix = blockIdx.x * C + c;
+  const cx<T> *col = reinterpret_cast<const cx<T> *>(a.scratch) + ((long)inst * 2 + comp) * (long)N * a.nx + ix;
+  const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
+  cx<T> v[1][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[0][m] = col[(long)(t + m * TT) * a.nx];
+  block_fft<LOGN, LOGE, -1, 1>(v, t, reinterpret_cast<const cx<T> *>(a.twy), acc);
+  const double kL = a.gpar[4 * inst + 3];
+  const double kx = a.dkx * kbin(ix, a.nx);
+  const double shift = (comp == 0 ? -kL : kL) * kx;
+  double s[1] = {0.0};
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const double ky = a.dky * kbin(t + m * TT, N);
+    const double re = v[0][m].re, im = v[0][m].im;
+    s[0] += (0.5 * (kx * kx + ky * ky) + shift) * (re * re + im * im);
+  }
+  block_sum<1>(s);
+  if (threadIdx.x == 0) a.partials[((long)inst * 2 + comp) * gridDim.x + blockIdx.x] = s[0];
+}
+
+// ---------------------------------------------------- generic reductions
+
+template <class T>
+__global__ void __launch_bounds__(256) norm_kernel(const cx<T> *__restrict__ psi, long plane,
+                                                   double *__restrict__ partials) {
+  const int inst = blockIdx.y;
+  const cx<T> *u = psi + (long)inst * 2 * plane, *d = u + plane;
+  double s[2] = {0.0, 0.0};
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (long)gridDim.x * blockDim.x) {
+    const cx<T> a = u[i], b = d[i];
+    s[0] += double(a.re) * a.re + double(a.im) * a.im;
+    s[1] += double(b.re) * b.re + double(b.im) * b.im;
+  }
+  block_sum<2>(s);
+  if (threadIdx.x == 0) {
+    partials[((long)inst * gridDim.x + blockIdx.x) * 2] = s[0];
+    partials[((long)inst * gridDim.x + blockIdx.x) * 2 + 1] = s[1];
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) residual_kernel(const cx<T> *__restrict__ psi, const cx<T> *__restrict__ prev,
+                                                       long plane, double *__restrict__ partials) {
+  const int inst = blockIdx.y;
+  const long base = (long)inst * 2 * plane;
+  double s[2] = {0.0, 0.0};
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * plane; i += (long)gridDim.x * blockDim.x) {
+    const cx<T> a = psi[base + i], b = prev[base + i];
+    const double dr = double(a.re) - b.re, di = double(a.im) - b.im;
+    s[0] += dr * dr + di * di;
+    s[1] += double(b.re) * b.re + double(b.im) * b.im;
+  }
+  block_sum<2>(s);
+  if (threadIdx.x == 0) {
+    partials[((long)inst * gridDim.x + blockIdx.x) * 2] = s[0];
+    partials[((long)inst * gridDim.x + blockIdx.x) * 2 + 1] = s[1];
+  }
+}
+
+// ------------------------------------------- comparator elementwise kernels
+
+// R(tau) = X D X at every point, as one separate Hadamard-style pass.
+template <class T, bool IMAG>
+__global__ void __launch_bounds__(256) ref_R_kernel(const RowArgs a) {
+  const long plane = (long)a.ny * a.nx;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int inst = blockIdx.y;
+  if (i >= plane) return;
+  const int y = int(i / a.nx), x = int(i - (long)y * a.nx);
+  cx<T> *u = reinterpret_cast<cx<T> *>(a.psi) + (long)inst * 2 * plane + i;
+  cx<T> *d = u + plane;
+  const q4<T> px = reinterpret_cast<const q4<T> *>(a.tabx)[(long)inst * a.nx + x];
+  const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
+  T vu = px.x + ty.x, vd = px.y + ty.y, c = px.z, s = px.w;
+  rot_compose<IMAG>(c, s, ty.z, ty.w);
+  if (a.pot2d) {
+    const q4<T> q = reinterpret_cast<const q4<T> *>(a.pot2d)[i];
+    vu += q.x;
+    vd += q.y;
+    T c2, s2;
+    rot_of<IMAG>(q.z * T(a.xang), c2, s2);
+    rot_compose<IMAG>(c, s, c2, s2);
+  }
+  cx<T> U = *u, D = *d;
+  opX<IMAG>(U, D, c, s);
+  opD<IMAG>(U, D, vu, vd, T(a.gpar[4 * inst]), T(a.gpar[4 * inst + 1]), T(a.gpar[4 * inst + 2]), T(a.tau));
+  opX<IMAG>(U, D, c, s);
+  *u = U;
+  *d = D;
+}
+
+// K(dt) with 1/(nx ny) on the transformed planes, as one separate pass.
+template <class T>
+__global__ void __launch_bounds__(256) ref_K_kernel(const ColArgs a) {
+  const long plane = (long)a.ny * a.nx;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int pc = blockIdx.y;  // inst * 2 + comp
+  if (i >= plane) return;
+  const int ky = int(i / a.nx), kx = int(i - (long)ky * a.nx);
+  cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (long)pc * plane + i;
+  const cx<T> f = cmul(reinterpret_cast<const cx<T> *>(a.kxt)[(long)pc * a.nx + kx],
+                       reinterpret_cast<const cx<T> *>(a.kyt)[ky]);
+  *p = cmul(*p, f);
+}
+
+}  // namespace spgpe

@@ -1,0 +1,86 @@
+// Row-pass launchers (included once per precision by kernels_row_f32.cu /
+// kernels_row_f64.cu).
+#pragma once
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace spgpe {
+
+// Elements per thread of the row pass: 16 complex64 or 8 complex128 values
+// per component (both components live in the same thread).
+template <class T> constexpr int row_loge(int logn) { return std::min(logn, sizeof(T) == 4 ? 4 : 3); }
+
+template <class T> LaunchShape row_shape(int nx, int ny) {
+  int logn = 0;
+  while ((1 << logn) < nx) ++logn;
+  const int E = 1 << row_loge<T>(logn);
+  const int TT = nx / E;
+  const int rows = std::max(1, std::min(kRowMaxThreads / TT, ny));
+  LaunchShape s;
+  s.elems_per_thread = E;
+  s.threads = rows * TT;
+  s.blocks_x = ny / rows;
+  s.rows_or_cols = rows;
+  s.smem = (size_t)rows * row_stride(nx, sizeof(cx<T>)) * sizeof(cx<T>);
+  return s;
+}
+
+template <class T, int LOGN, int F> cudaError_t row_launch_n(RowArgs a, cudaStream_t st) {
+  constexpr int LOGE = row_loge<T>(LOGN);
+  auto kern = row_pass<T, LOGN, LOGE, F>;
+  const LaunchShape sh = row_shape<T>(a.nx, a.ny);
+  static int attr_set = 0;  // largest dynamic shared memory granted so far
+  if ((int)sh.smem > attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    if (e != cudaSuccess) return e;
+    attr_set = (int)sh.smem;
+  }
+  a.rows = sh.rows_or_cols;
+  kern<<<dim3(sh.blocks_x, a.ninst), sh.threads, sh.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T, int LOGN> cudaError_t row_launch_f(int flags, const RowArgs &a, cudaStream_t st) {
+  switch (flags) {
+    case kRealFirst: return row_launch_n<T, LOGN, kRealFirst>(a, st);
+    case kRealMid: return row_launch_n<T, LOGN, kRealMid>(a, st);
+    case kRealLast: return row_launch_n<T, LOGN, kRealLast>(a, st);
+    case kImagFirst: return row_launch_n<T, LOGN, kImagFirst>(a, st);
+    case kImagB: return row_launch_n<T, LOGN, kImagB>(a, st);
+    case kImagA: return row_launch_n<T, LOGN, kImagA>(a, st);
+    case kImagScale: return row_launch_n<T, LOGN, kImagScale>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T> cudaError_t launch_row(int flags, RowArgs a, cudaStream_t st) {
+  switch (a.nx) {
+    case 8: return row_launch_f<T, 3>(flags, a, st);
+    case 16: return row_launch_f<T, 4>(flags, a, st);
+    case 32: return row_launch_f<T, 5>(flags, a, st);
+    case 64: return row_launch_f<T, 6>(flags, a, st);
+    case 128: return row_launch_f<T, 7>(flags, a, st);
+    case 256: return row_launch_f<T, 8>(flags, a, st);
+    case 512: return row_launch_f<T, 9>(flags, a, st);
+    case 1024: return row_launch_f<T, 10>(flags, a, st);
+    case 2048: return row_launch_f<T, 11>(flags, a, st);
+    case 4096: return row_launch_f<T, 12>(flags, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStream_t st) {
+  const long plane = (long)a.nx * a.ny;
+  const dim3 grid((unsigned)((plane + 255) / 256), a.ninst);
+  if (imag) ref_R_kernel<T, true><<<grid, 256, 0, st>>>(a);
+  else ref_R_kernel<T, false><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define SPGPE_INSTANTIATE_ROW(T)                                                    \
+  template LaunchShape row_shape<T>(int, int);                                      \
+  template cudaError_t launch_row<T>(int, RowArgs, cudaStream_t);                   \
+  template cudaError_t launch_ref_R<T>(bool, const RowArgs &, cudaStream_t);
+
+}  // namespace spgpe

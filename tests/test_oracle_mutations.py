@@ -64,7 +64,7 @@ def test_pins_kill_mutant(tmp_path, name):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
     os.makedirs(tmp_path / "paper_2010_15069_gb300")
-    for f in ("__init__.py", "inputs.py"):
+    for f in ("__init__.py", "_lib.py", "inputs.py"):
         shutil.copy(os.path.join(ROOT, "paper_2010_15069_gb300", f), tmp_path / "paper_2010_15069_gb300" / f)
     (tmp_path / "oracle" / "spgpe_oracle.cpp").write_text(src)
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
