@@ -159,18 +159,40 @@ int upload_raw(spgpe_ctx *c) {
   return SPGPE_OK;
 }
 
-// Step tables for substep dt (real or imaginary time):
-//   x/y step tables {V + delta/2, V - delta/2, c, s} of the separable pieces,
-//   (c, s) = (cos, sin) or (cosh, sinh) of Omega_piece * dt / 8 (X(dt/4));
-//   K tables a_j(kx) = exp(-i dt (kx^2/2 -+ kL kx)), b(ky) = exp(-i dt ky^2/2)/(nx ny)
-//   (imaginary time: the real exponentials exp(-dt (...))).
+// Step tables for substep dt (real or imaginary time).  Unit-modulus factors
+// are stored as (f - 1) to full relative precision (the kernels apply
+// z + (f - 1) z):
+//   x/y step tables {V + delta/2, V - delta/2, m, s} of the separable pieces,
+//   (m, s) = (cos a - 1, sin a) or (cosh a - 1, sinh a), a = Omega_piece dt / 8
+//   (the angle of X(dt/4));
+//   K tables a_j(kx) - 1 with a_j = exp(-i dt (kx^2/2 -+ kL kx)) and b(ky) - 1
+//   with b = exp(-i dt ky^2/2) (imaginary time: exp(-dt (...)) - 1); the
+//   1/(nx ny) of the inverse transform is applied in the kernel.
 int ensure_tables(spgpe_ctx *c, double dt, int imag) {
   if (c->tab_dt == dt && c->tab_imag == imag) return SPGPE_OK;
   const int nx = c->nx, ny = c->ny, ni = c->ninst;
   std::vector<double> tx((size_t)ni * nx * 4), ty((size_t)ni * ny * 4);
-  auto rot = [&](double ang, double &cc, double &ss) {
-    if (imag) { cc = std::cosh(ang); ss = std::sinh(ang); }
-    else { cc = std::cos(ang); ss = std::sin(ang); }
+  auto rot = [&](double ang, double &mm, double &ss) {
+    if (imag) {
+      const double sh = std::sinh(0.5 * ang);
+      mm = 2.0 * sh * sh;
+      ss = std::sinh(ang);
+    } else {
+      const double sh = std::sin(0.5 * ang);
+      mm = -2.0 * sh * sh;
+      ss = std::sin(ang);
+    }
+  };
+  // exp(-i th) - 1 (real time) or exp(-th) - 1 (imaginary time)
+  auto em1 = [&](double th, double *o) {
+    if (imag) {
+      o[0] = std::expm1(-th);
+      o[1] = 0.0;
+    } else {
+      const double sh = std::sin(0.5 * th);
+      o[0] = -2.0 * sh * sh;
+      o[1] = -std::sin(th);
+    }
   };
   for (int i = 0; i < ni; ++i) {
     for (int x = 0; x < nx; ++x) {
@@ -189,23 +211,17 @@ int ensure_tables(spgpe_ctx *c, double dt, int imag) {
     }
   }
   std::vector<double> kx((size_t)ni * 2 * nx * 2), ky((size_t)ny * 2);
-  const double inv = 1.0 / ((double)nx * ny);
   for (int i = 0; i < ni; ++i) {
     const double kL = c->hg[4 * i + 3];
     for (int j = 0; j < 2; ++j)
       for (int x = 0; x < nx; ++x) {
         const double k = kval(x, nx, c->dx);
-        const double T = 0.5 * k * k + (j == 0 ? -kL : kL) * k;
-        double *o = &kx[(((size_t)i * 2 + j) * nx + x) * 2];
-        if (imag) { o[0] = std::exp(-dt * T); o[1] = 0.0; }
-        else { o[0] = std::cos(dt * T); o[1] = -std::sin(dt * T); }
+        em1(dt * (0.5 * k * k + (j == 0 ? -kL : kL) * k), &kx[(((size_t)i * 2 + j) * nx + x) * 2]);
       }
   }
   for (int y = 0; y < ny; ++y) {
     const double k = kval(y, ny, c->dy);
-    const double T = 0.5 * k * k;
-    if (imag) { ky[2 * y] = inv * std::exp(-dt * T); ky[2 * y + 1] = 0.0; }
-    else { ky[2 * y] = inv * std::cos(dt * T); ky[2 * y + 1] = -inv * std::sin(dt * T); }
+    em1(dt * 0.5 * k * k, &ky[2 * (size_t)y]);
   }
   int r;
   if ((r = upload(c, c->d_tabx, tx)) || (r = upload(c, c->d_taby, ty)) || (r = upload(c, c->d_kxt, kx)) ||

@@ -26,8 +26,8 @@ constexpr int kImagScale = F_IMAG | F_SCALE;
 // Arguments of the fused row pass (x direction, both components per thread).
 struct RowArgs {
   void *psi;              // [ninst][2][ny][nx] complex, in place
-  const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, c, s} step table
-  const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, c, s} step table
+  const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, cos-1, sin} step table
+  const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, cos-1, sin} step table
   const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
   const void *tw;         // [nx] forward roots exp(-2 pi i m / nx)
   const double *gpar;     // [ninst][4] {g11, g22, g12, kL}
@@ -46,8 +46,8 @@ struct RowArgs {
 // Arguments of the fused column pass (y direction, one component per block).
 struct ColArgs {
   void *psi;
-  const void *kxt;        // [ninst][2][nx] complex factor a_j(kx)
-  const void *kyt;        // [ny] complex factor b(ky), includes 1/(nx ny)
+  const void *kxt;        // [ninst][2][nx] complex a_j(kx) - 1
+  const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
   const void *tw;         // [ny] forward roots
   int nx, ny, ninst, C;
 };

@@ -28,59 +28,85 @@ struct alignas(4 * sizeof(T)) q4 {
 
 // ------------------------------------------------------------ math helpers
 
-template <class T> __device__ __forceinline__ T d_exp(T a) {
-  if constexpr (std::is_same<T, float>::value) return expf(a); else return exp(a);
+template <class T> __device__ __forceinline__ T d_fma(T a, T b, T c) {
+  if constexpr (std::is_same<T, float>::value) return fmaf(a, b, c); else return fma(a, b, c);
+}
+template <class T> __device__ __forceinline__ T d_expm1(T a) {
+  if constexpr (std::is_same<T, float>::value) return expm1f(a); else return expm1(a);
 }
 template <class T> __device__ __forceinline__ void d_sincos(T a, T *s, T *c) {
   if constexpr (std::is_same<T, float>::value) sincosf(a, s, c); else sincos(a, s, c);
-}
-template <class T> __device__ __forceinline__ T d_cosh(T a) {
-  if constexpr (std::is_same<T, float>::value) return coshf(a); else return cosh(a);
 }
 template <class T> __device__ __forceinline__ T d_sinh(T a) {
   if constexpr (std::is_same<T, float>::value) return sinhf(a); else return sinh(a);
 }
 
-// Rotation coefficients of X for an angle: (cos, sin) in real time, (cosh,
-// sinh) in imaginary time; compose() adds two angles.
-template <bool IMAG, class T> __device__ __forceinline__ void rot_of(T ang, T &c, T &s) {
-  if constexpr (IMAG) { c = d_cosh(ang); s = d_sinh(ang); } else { d_sincos(ang, &s, &c); }
-}
-template <bool IMAG, class T> __device__ __forceinline__ void rot_compose(T &c, T &s, T c2, T s2) {
-  const T nc = IMAG ? c * c2 + s * s2 : c * c2 - s * s2;
-  const T ns = s * c2 + c * s2;
-  c = nc;
-  s = ns;
-}
+// Every unit-modulus factor of the step (the D phase, the Raman rotation X,
+// the kinetic factor K) is applied as z + (f - 1) z with f - 1 evaluated to
+// full relative precision (f - 1 = -2 sin^2(h) + 2i sin(h) cos(h), h the half
+// phase; expm1 in imaginary time).  Multiplying by a rounded (cos, sin) pair
+// instead would change |z| by a fixed, phase-dependent amount each step; those
+// errors are systematic for slowly varying phases and add up over thousands
+// of steps.  The operations are written with explicit fma so that every
+// kernel that applies them rounds identically.
 
-// X: (u, d) <- exp(-i theta sigma_x) (u, d), theta the half-angle whose
-// (cos, sin) are (c, s); imaginary time exp(-theta sigma_x) with (cosh, sinh).
-template <bool IMAG, class T> __device__ __forceinline__ void opX(cx<T> &u, cx<T> &d, T c, T s) {
-  const cx<T> a = u, b = d;
+// (cos(a) - 1, sin(a)) of a rotation angle, or (cosh(a) - 1, sinh(a)).
+template <bool IMAG, class T> __device__ __forceinline__ void rot_of(T ang, T &m, T &s) {
   if constexpr (IMAG) {
-    u = {c * a.re - s * b.re, c * a.im - s * b.im};
-    d = {c * b.re - s * a.re, c * b.im - s * a.im};
+    const T sh = d_sinh(T(0.5) * ang);
+    m = T(2) * sh * sh;
+    s = d_sinh(ang);
   } else {
-    u = {c * a.re + s * b.im, c * a.im - s * b.re};
-    d = {c * b.re + s * a.im, c * b.im - s * a.re};
+    T sh, ch;
+    d_sincos(T(0.5) * ang, &sh, &ch);
+    m = T(-2) * sh * sh;
+    s = T(2) * sh * ch;
   }
 }
 
-// D(tau): diagonal potential + mean-field phase (decay), densities on entry.
-template <bool IMAG, class T>
-__device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T tau) {
-  const T ru = cabs2(u), rd = cabs2(d);
-  const T eu = vu + g11 * ru + g12 * rd;
-  const T ed = vd + g22 * rd + g12 * ru;
+// Angle addition in the (c - 1, s) representation.
+template <bool IMAG, class T> __device__ __forceinline__ void rot_compose(T &m, T &s, T m2, T s2) {
+  const T nm = d_fma(m, m2, d_fma(IMAG ? s : -s, s2, m + m2));
+  const T ns = d_fma(s, m2, d_fma(s2, m, s + s2));
+  m = nm;
+  s = ns;
+}
+
+// X: (u, d) <- exp(-i theta sigma_x) (u, d) with (m, s) = (cos theta - 1, sin theta);
+// imaginary time exp(-theta sigma_x) with (cosh theta - 1, sinh theta).
+template <bool IMAG, class T> __device__ __forceinline__ void opX(cx<T> &u, cx<T> &d, T m, T s) {
+  const cx<T> a = u, b = d;
   if constexpr (IMAG) {
-    u = cscale(u, d_exp(-tau * eu));
-    d = cscale(d, d_exp(-tau * ed));
+    u = {d_fma(m, a.re, d_fma(-s, b.re, a.re)), d_fma(m, a.im, d_fma(-s, b.im, a.im))};
+    d = {d_fma(m, b.re, d_fma(-s, a.re, b.re)), d_fma(m, b.im, d_fma(-s, a.im, b.im))};
+  } else {
+    u = {d_fma(m, a.re, d_fma(s, b.im, a.re)), d_fma(m, a.im, d_fma(-s, b.re, a.im))};
+    d = {d_fma(m, b.re, d_fma(s, a.im, b.re)), d_fma(m, b.im, d_fma(-s, a.re, b.im))};
+  }
+}
+
+// z <- z + z w for a complex w = f - 1.
+template <class T> __device__ __forceinline__ cx<T> add_mul1(cx<T> z, cx<T> w) {
+  return {d_fma(z.re, w.re, d_fma(-z.im, w.im, z.re)), d_fma(z.re, w.im, d_fma(z.im, w.re, z.im))};
+}
+
+// D(tau): diagonal potential + mean-field phase (decay), densities on entry.
+// htau = -tau/2 in real time (the half phase), -tau in imaginary time.
+template <bool IMAG, class T>
+__device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T htau) {
+  const T ru = d_fma(u.re, u.re, u.im * u.im), rd = d_fma(d.re, d.re, d.im * d.im);
+  const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
+  const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
+  if constexpr (IMAG) {
+    const T fu = d_expm1(htau * eu), fd = d_expm1(htau * ed);
+    u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
+    d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
   } else {
     T su, cu, sd, cd;
-    d_sincos(-tau * eu, &su, &cu);
-    d_sincos(-tau * ed, &sd, &cd);
-    u = cmul(u, cx<T>{cu, su});
-    d = cmul(d, cx<T>{cd, sd});
+    d_sincos(htau * eu, &su, &cu);
+    d_sincos(htau * ed, &sd, &cd);
+    u = add_mul1(u, cx<T>{T(-2) * su * su, T(2) * su * cu});
+    d = add_mul1(d, cx<T>{T(-2) * sd * sd, T(2) * sd * cd});
   }
 }
 
@@ -166,7 +192,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxT
     const q4<T> *tx = reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
     const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
     const T g11 = T(a.gpar[4 * inst]), g22 = T(a.gpar[4 * inst + 1]), g12 = T(a.gpar[4 * inst + 2]);
-    const T tau = T(a.tau), xang = T(a.xang);
+    const T htau = T(IMAG ? -a.tau : -0.5 * a.tau), xang = T(a.xang);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int x = t + m * TT;
@@ -191,7 +217,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxT
         }
         if constexpr (F & F_REND) {
           opX<IMAG>(u, d, c, s);
-          opD<IMAG>(u, d, vu, vd, g11, g22, g12, tau);
+          opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
           opX<IMAG>(u, d, c, s);
         }
         if constexpr (F & F_PART) {
@@ -200,7 +226,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxT
         }
         if constexpr (F & F_RSTART) {
           opX<IMAG>(u, d, c, s);
-          opD<IMAG>(u, d, vu, vd, g11, g22, g12, tau);
+          opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
           opX<IMAG>(u, d, c, s);
         }
       }
@@ -272,16 +298,24 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
 #pragma unroll
   for (int m = 0; m < E; ++m) v[0][m] = col[(long)(t + m * TT) * a.nx];
   block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);
-  const cx<T> ax = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
-  const cx<T> *by = reinterpret_cast<const cx<T> *>(a.kyt);
+  // K(dt) = a_j(kx) b(ky) / (nx ny) as z + (K' - 1) z, K' - 1 = (a-1)(b-1) + (a-1) + (b-1);
+  // the exact power of two 1/(nx ny) is applied last.
+  const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
+  const cx<T> *bm = reinterpret_cast<const cx<T> *>(a.kyt);
+  const T inv = T(1) / T((long)a.nx * N);
 #pragma unroll
   for (int m = 0; m < E; ++m) {
-    const cx<T> b = by[t + m * TT];
+    const cx<T> b = bm[t + m * TT];
+    cx<T> z = v[0][m];
     if constexpr (IMAG) {
-      v[0][m] = cscale(v[0][m], ax.re * b.re);
+      const T k1 = d_fma(am.re, b.re, am.re + b.re);
+      z = {d_fma(z.re, k1, z.re), d_fma(z.im, k1, z.im)};
     } else {
-      v[0][m] = cmul(v[0][m], cmul(ax, b));
+      const cx<T> k1 = {d_fma(am.re, b.re, d_fma(-am.im, b.im, am.re + b.re)),
+                        d_fma(am.re, b.im, d_fma(am.im, b.re, am.im + b.im))};
+      z = add_mul1(z, k1);
     }
+    v[0][m] = {z.re * inv, z.im * inv};
   }
   block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
 #pragma unroll
@@ -445,7 +479,8 @@ __global__ void __launch_bounds__(256) ref_R_kernel(const RowArgs a) {
   }
   cx<T> U = *u, D = *d;
   opX<IMAG>(U, D, c, s);
-  opD<IMAG>(U, D, vu, vd, T(a.gpar[4 * inst]), T(a.gpar[4 * inst + 1]), T(a.gpar[4 * inst + 2]), T(a.tau));
+  opD<IMAG>(U, D, vu, vd, T(a.gpar[4 * inst]), T(a.gpar[4 * inst + 1]), T(a.gpar[4 * inst + 2]),
+            T(IMAG ? -a.tau : -0.5 * a.tau));
   opX<IMAG>(U, D, c, s);
   *u = U;
   *d = D;
@@ -460,9 +495,13 @@ __global__ void __launch_bounds__(256) ref_K_kernel(const ColArgs a) {
   if (i >= plane) return;
   const int ky = int(i / a.nx), kx = int(i - (long)ky * a.nx);
   cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (long)pc * plane + i;
-  const cx<T> f = cmul(reinterpret_cast<const cx<T> *>(a.kxt)[(long)pc * a.nx + kx],
-                       reinterpret_cast<const cx<T> *>(a.kyt)[ky]);
-  *p = cmul(*p, f);
+  const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[(long)pc * a.nx + kx];
+  const cx<T> b = reinterpret_cast<const cx<T> *>(a.kyt)[ky];
+  const cx<T> k1 = {d_fma(am.re, b.re, d_fma(-am.im, b.im, am.re + b.re)),
+                    d_fma(am.re, b.im, d_fma(am.im, b.re, am.im + b.im))};
+  const T inv = T(1) / T(plane);
+  const cx<T> z = add_mul1(*p, k1);
+  *p = {z.re * inv, z.im * inv};
 }
 
 }  // namespace spgpe

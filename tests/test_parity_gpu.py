@@ -60,9 +60,10 @@ def model_for(orc, p):
                      g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
 
 
-def coupled(nx, ny, L=8.0, g=60.0):
-    """All terms on: trap, detuning gradient, uniform Raman, SOC, unequal couplings."""
-    return inputs.problem(nx, ny, L, L * ny / nx if nx != ny else L, Omega=1.7, delta_slope=0.3,
+def coupled(nx, ny, g=60.0):
+    """All terms on: trap, detuning gradient, uniform Raman, SOC, unequal couplings.
+    Grid spacing 0.25 in both directions (box at least [-2, 2])."""
+    return inputs.problem(nx, ny, max(2.0, 0.125 * nx), max(2.0, 0.125 * ny), Omega=1.7, delta_slope=0.3,
                           g11=g, g22=0.8 * g, g12=0.9 * g, kL=0.9)
 
 
