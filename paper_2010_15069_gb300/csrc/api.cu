@@ -129,7 +129,38 @@ void free_all(spgpe_ctx *c) {
   if (c->plan_ok) cufftDestroy(c->plan);
 }
 
-// Forward roots exp(-2 pi i m / n), FP64 then rounded once.
+// Forward roots exp(-2 pi i m / n) in single precision.  Of the nine float
+// pairs within one ulp of the rounded (cos, sin), take the one whose squared
+// modulus is closest to one (evaluated exactly in double): the transforms use
+// each root at every step, so a modulus error that always has the same sign
+// would scale the spinor by a fixed factor per step.
+std::vector<float> roots_f32(int n) {
+  std::vector<float> w(2 * (size_t)n);
+  for (int m = 0; m < n; ++m) {
+    const double c = std::cos(kTwoPi * m / n), s = -std::sin(kTwoPi * m / n);
+    const float cf = (float)c, sf = (float)s;
+    float best_c = cf, best_s = sf;
+    double best = 1e300, best_ph = 1e300;
+    for (int i = -1; i <= 1; ++i)
+      for (int j = -1; j <= 1; ++j) {
+        const float cc = i < 0 ? std::nextafter(cf, -2.0f) : i > 0 ? std::nextafter(cf, 2.0f) : cf;
+        const float ss = j < 0 ? std::nextafter(sf, -2.0f) : j > 0 ? std::nextafter(sf, 2.0f) : sf;
+        const double mod = std::fabs((double)cc * cc + (double)ss * ss - 1.0);
+        const double ph = std::fabs((double)cc - c) + std::fabs((double)ss - s);
+        if (mod < best || (mod == best && ph < best_ph)) {
+          best = mod;
+          best_ph = ph;
+          best_c = cc;
+          best_s = ss;
+        }
+      }
+    w[2 * m] = best_c;
+    w[2 * m + 1] = best_s;
+  }
+  return w;
+}
+
+// Forward roots exp(-2 pi i m / n), FP64.
 std::vector<double> roots(int n) {
   std::vector<double> w(2 * (size_t)n);
   for (int m = 0; m < n; ++m) {
@@ -418,7 +449,17 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
     delete c;
     return SPGPE_ECUDA;
   }
-  if ((r = upload(c, c->d_twx, roots(nx))) || (r = upload(c, c->d_twy, roots(ny)))) {
+  if (dtype == SPGPE_C64) {
+    const std::vector<float> wx = roots_f32(nx), wy = roots_f32(ny);
+    if (cudaMemcpyAsync(c->d_twx, wx.data(), wx.size() * sizeof(float), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_twy, wy.data(), wy.size() * sizeof(float), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      r = SPGPE_ECUDA, c->err = "twiddle upload failed";
+    else
+      r = SPGPE_OK;
+  } else if (!(r = upload(c, c->d_twx, roots(nx)))) {
+    r = upload(c, c->d_twy, roots(ny));
+  }
+  if (r) {
     g_init_error = c->err;
     free_all(c);
     delete c;

@@ -24,6 +24,9 @@ struct alignas(2 * sizeof(T)) cx {
   T re, im;
 };
 
+template <class T> __device__ __forceinline__ T d_fma(T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) return fmaf(a, b, c); else return fma(a, b, c);
+}
 template <class T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
 template <class T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
 template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
@@ -32,29 +35,44 @@ template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
 template <class T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.re * s, a.im * s}; }
 template <class T> __device__ __forceinline__ T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 
-// a * exp(SIGN * 2 pi i M / 16) for a compile-time M in [0, 8).  The cosines
-// and sines of multiples of pi/8 are written out to 20 digits and rounded
-// once to T.
+// Rotation of a by the angle phi with tan(phi/2) = t and sin(phi) = s, as
+// three shears (x -= t y; y += s x; x -= t y).  Each shear has determinant
+// one whatever the rounding of t and s, so the rotation never scales |a|
+// systematically; a rounded (cos, sin) pair would scale it by a fixed factor
+// 1 + O(2^-24) at every use, which accumulates over thousands of transforms.
+template <class T> __device__ __forceinline__ cx<T> shear_rot(cx<T> a, T t, T s) {
+  const T x1 = d_fma(-t, a.im, a.re);
+  const T y1 = d_fma(s, x1, a.im);
+  return {d_fma(-t, y1, x1), y1};
+}
+
+// a * exp(SIGN * 2 pi i M / 16) for a compile-time M in [0, 8): quarter turns
+// are exact (swap and negate), the rest is a three-shear rotation by +-pi/8 or
+// +-pi/4.  Constants: tan(pi/16), sin(pi/8), tan(pi/8), sin(pi/4) to 20 digits,
+// rounded once to T.
 template <int SIGN, int M, class T>
 __device__ __forceinline__ cx<T> w16(cx<T> a) {
-  constexpr double C1 = 0.92387953251128675613;  // cos(pi/8)
-  constexpr double S1 = 0.38268343236508977173;  // sin(pi/8)
-  constexpr double H = 0.70710678118654752440;   // cos(pi/4)
-  const T c1 = T(C1), s1 = T(S1), h = T(H);
+  const T t16 = T(0.19891236737965800691), s8 = T(0.38268343236508977173);
+  const T t8 = T(0.41421356237309504880), s4 = T(0.70710678118654752440);
   const T sg = T(SIGN);
+  auto qturn = [&](cx<T> b) { return cx<T>{-sg * b.im, sg * b.re}; };  // * SIGN i
   if constexpr (M == 0) {
     return a;
-  } else if constexpr (M == 4) {
-    return {-sg * a.im, sg * a.re};
+  } else if constexpr (M == 1) {
+    return shear_rot(a, sg * t16, sg * s8);
   } else if constexpr (M == 2) {
-    return {(a.re - sg * a.im) * h, (a.im + sg * a.re) * h};
+    return shear_rot(a, sg * t8, sg * s4);
+  } else if constexpr (M == 3) {
+    return qturn(shear_rot(a, -sg * t16, -sg * s8));
+  } else if constexpr (M == 4) {
+    return qturn(a);
+  } else if constexpr (M == 5) {
+    return qturn(shear_rot(a, sg * t16, sg * s8));
   } else if constexpr (M == 6) {
-    return {(-a.re - sg * a.im) * h, (-a.im + sg * a.re) * h};
+    return qturn(shear_rot(a, sg * t8, sg * s4));
   } else {
-    // cos/sin of M*pi/8 for M = 1, 3, 5, 7
-    const T c = (M == 1) ? c1 : (M == 3) ? s1 : (M == 5) ? -s1 : -c1;
-    const T s = sg * ((M == 1 || M == 7) ? s1 : c1);
-    return {a.re * c - a.im * s, a.re * s + a.im * c};
+    const cx<T> b = shear_rot(a, -sg * t16, -sg * s8);
+    return {-b.re, -b.im};
   }
 }
 

@@ -16,6 +16,7 @@
 
 #include <type_traits>
 
+#include "fastmath.cuh"
 #include "fft_core.cuh"
 #include "internal.h"
 
@@ -28,19 +29,6 @@ struct alignas(4 * sizeof(T)) q4 {
 
 // ------------------------------------------------------------ math helpers
 
-template <class T> __device__ __forceinline__ T d_fma(T a, T b, T c) {
-  if constexpr (std::is_same<T, float>::value) return fmaf(a, b, c); else return fma(a, b, c);
-}
-template <class T> __device__ __forceinline__ T d_expm1(T a) {
-  if constexpr (std::is_same<T, float>::value) return expm1f(a); else return expm1(a);
-}
-template <class T> __device__ __forceinline__ void d_sincos(T a, T *s, T *c) {
-  if constexpr (std::is_same<T, float>::value) sincosf(a, s, c); else sincos(a, s, c);
-}
-template <class T> __device__ __forceinline__ T d_sinh(T a) {
-  if constexpr (std::is_same<T, float>::value) return sinhf(a); else return sinh(a);
-}
-
 // Every unit-modulus factor of the step (the D phase, the Raman rotation X,
 // the kinetic factor K) is applied as z + (f - 1) z with f - 1 evaluated to
 // full relative precision (f - 1 = -2 sin^2(h) + 2i sin(h) cos(h), h the half
@@ -50,17 +38,15 @@ template <class T> __device__ __forceinline__ T d_sinh(T a) {
 // of steps.  The operations are written with explicit fma so that every
 // kernel that applies them rounds identically.
 
-// (cos(a) - 1, sin(a)) of a rotation angle, or (cosh(a) - 1, sinh(a)).
+// (cos(a) - 1, sin(a)) of a rotation angle, or (cosh(a) - 1, sinh(a)), to full
+// relative precision: cosh(a) - 1 = 2 sinh^2(a/2), sinh(b) = (expm1(b) - expm1(-b))/2.
 template <bool IMAG, class T> __device__ __forceinline__ void rot_of(T ang, T &m, T &s) {
   if constexpr (IMAG) {
-    const T sh = d_sinh(T(0.5) * ang);
-    m = T(2) * sh * sh;
-    s = d_sinh(ang);
+    const T hh = T(0.5) * (expm1_f(T(0.5) * ang) - expm1_f(T(-0.5) * ang));
+    m = T(2) * hh * hh;
+    s = T(0.5) * (expm1_f(ang) - expm1_f(-ang));
   } else {
-    T sh, ch;
-    d_sincos(T(0.5) * ang, &sh, &ch);
-    m = T(-2) * sh * sh;
-    s = T(2) * sh * ch;
+    expi2_m1(T(0.5) * ang, m, s);
   }
 }
 
@@ -98,15 +84,15 @@ __device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22
   const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
   const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
   if constexpr (IMAG) {
-    const T fu = d_expm1(htau * eu), fd = d_expm1(htau * ed);
+    const T fu = expm1_f(htau * eu), fd = expm1_f(htau * ed);
     u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
     d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
   } else {
-    T su, cu, sd, cd;
-    d_sincos(htau * eu, &su, &cu);
-    d_sincos(htau * ed, &sd, &cd);
-    u = add_mul1(u, cx<T>{T(-2) * su * su, T(2) * su * cu});
-    d = add_mul1(d, cx<T>{T(-2) * sd * sd, T(2) * sd * cd});
+    cx<T> wu, wd;
+    expi2_m1(htau * eu, wu.re, wu.im);
+    expi2_m1(htau * ed, wd.re, wd.im);
+    u = add_mul1(u, wu);
+    d = add_mul1(d, wd);
   }
 }
 
@@ -157,79 +143,100 @@ template <class T> struct ColAcc {
 };
 
 // ------------------------------------------------------------- row pass
+//
+// Each row is held by 2*TT threads: TT threads per component, E values each.
+// Within a warp the two components sit in lane groups `half` apart (lanes
+// 0..half-1 component up, the next half lanes component down, repeated), so
+// the partner holding the other component of the same positions is lane ^ half.
+// The transforms run on one component per thread.  For the pointwise R
+// operator, which needs both components of a point, partners swap half of
+// their values with shuffles: the up-thread then owns positions m < E/2 of
+// both components, the down-thread positions m >= E/2; they swap back after.
 
 template <class T, int LOGN, int LOGE, int F>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxThreads) row_pass(const RowArgs a) {
-  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+__global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass(const RowArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
   constexpr bool IMAG = (F & F_IMAG) != 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
-  const int lrow = threadIdx.x / TT, t = threadIdx.x - lrow * TT;
+  const int half = min(16, (int)blockDim.x / 2);
+  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  const int tx = threadIdx.x;
+  const int comp = (tx / half) & 1;
+  const int tp = (tx % half) + half * (tx / (2 * half));
+  const int lrow = tp / TT, t = tp - lrow * TT;
   const int inst = blockIdx.y;
   const int y = blockIdx.x * a.rows + lrow;
-  const long plane = (long)a.ny * N;
-  cx<T> *up = reinterpret_cast<cx<T> *>(a.psi) + (long)inst * 2 * plane + (long)y * N;
-  cx<T> *dn = up + plane;
+  cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N;
   const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
-  const RowAcc<T> acc{sm + lrow * row_stride(N, sizeof(cx<T>)), row_pad_n(N, sizeof(cx<T>))};
+  constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
+  const RowAcc<T> acc{sm + lrow * row_stride(N, sizeof(cx<T>)) + comp * PADN, 0};
 
-  cx<T> v[2][E];
+  cx<T> v[1][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    v[0][m] = up[t + m * TT];
-    v[1][m] = dn[t + m * TT];
+  for (int m = 0; m < E; ++m) v[0][m] = p[t + m * TT];
+  if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
+  if constexpr (F & F_SCALE) {
+    const T sc = T(a.scale[2 * inst + comp]);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[0][m] = cscale(v[0][m], sc);
   }
-  if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 2>(v, t, tw, acc);
 
   double nsum[2] = {0.0, 0.0};
-  if constexpr (F & (F_REND | F_RSTART | F_SCALE)) {
-    T sc0 = T(1), sc1 = T(1);
-    if constexpr (F & F_SCALE) {
-      sc0 = T(a.scale[2 * inst]);
-      sc1 = T(a.scale[2 * inst + 1]);
+  if constexpr (F & (F_REND | F_RSTART)) {
+    // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
+    cx<T> pu[H], pd[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const cx<T> snd = comp ? v[0][j] : v[0][H + j];
+      const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
+      pu[j] = comp ? rcv : v[0][j];
+      pd[j] = comp ? v[0][H + j] : rcv;
     }
     const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
-    const q4<T> *tx = reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
+    const q4<T> *tx4 = reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
     const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
     const T g11 = T(a.gpar[4 * inst]), g22 = T(a.gpar[4 * inst + 1]), g12 = T(a.gpar[4 * inst + 2]);
     const T htau = T(IMAG ? -a.tau : -0.5 * a.tau), xang = T(a.xang);
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int x = t + m * TT;
-      cx<T> &u = v[0][m];
-      cx<T> &d = v[1][m];
-      if constexpr (F & F_SCALE) {
-        u = cscale(u, sc0);
-        d = cscale(d, sc1);
+    for (int j = 0; j < H; ++j) {
+      const int x = t + (j + comp * H) * TT;
+      cx<T> &u = pu[j];
+      cx<T> &d = pd[j];
+      const q4<T> px = tx4[x];
+      T vu = px.x + ty.x, vd = px.y + ty.y;
+      T c = px.z, s = px.w;
+      rot_compose<IMAG>(c, s, ty.z, ty.w);
+      if (p2) {
+        const q4<T> q = p2[(long)y * N + x];
+        vu += q.x;
+        vd += q.y;
+        T c2, s2;
+        rot_of<IMAG>(q.z * xang, c2, s2);
+        rot_compose<IMAG>(c, s, c2, s2);
       }
-      if constexpr (F & (F_REND | F_RSTART)) {
-        const q4<T> px = tx[x];
-        T vu = px.x + ty.x, vd = px.y + ty.y;
-        T c = px.z, s = px.w;
-        rot_compose<IMAG>(c, s, ty.z, ty.w);
-        if (p2) {
-          const q4<T> q = p2[(long)y * N + x];
-          vu += q.x;
-          vd += q.y;
-          T c2, s2;
-          rot_of<IMAG>(q.z * xang, c2, s2);
-          rot_compose<IMAG>(c, s, c2, s2);
-        }
-        if constexpr (F & F_REND) {
-          opX<IMAG>(u, d, c, s);
-          opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
-          opX<IMAG>(u, d, c, s);
-        }
-        if constexpr (F & F_PART) {
-          nsum[0] += double(cabs2(u));
-          nsum[1] += double(cabs2(d));
-        }
-        if constexpr (F & F_RSTART) {
-          opX<IMAG>(u, d, c, s);
-          opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
-          opX<IMAG>(u, d, c, s);
-        }
+      if constexpr (F & F_REND) {
+        opX<IMAG>(u, d, c, s);
+        opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
+        opX<IMAG>(u, d, c, s);
       }
+      if constexpr (F & F_PART) {
+        nsum[0] += double(cabs2(u));
+        nsum[1] += double(cabs2(d));
+      }
+      if constexpr (F & F_RSTART) {
+        opX<IMAG>(u, d, c, s);
+        opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
+        opX<IMAG>(u, d, c, s);
+      }
+    }
+    // scatter back to one component per thread
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const cx<T> snd = comp ? pu[j] : pd[j];
+      const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
+      v[0][j] = comp ? rcv : pu[j];
+      v[0][H + j] = comp ? pd[j] : rcv;
     }
   }
 
@@ -272,12 +279,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxT
     }
   }
 
-  if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 2>(v, t, tw, acc);
+  if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    up[t + m * TT] = v[0][m];
-    dn[t + m * TT] = v[1][m];
-  }
+  for (int m = 0; m < E; ++m) p[t + m * TT] = v[0][m];
 }
 
 // ---------------------------------------------------------- column pass
@@ -293,10 +297,11 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
   cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + ((long)inst * 2 + comp) * (long)N * a.nx + kx;
   const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
   const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
+  const int rs = TT * a.nx;  // element offset between a thread's rows (fits in 32 bits)
 
   cx<T> v[1][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[0][m] = col[(long)(t + m * TT) * a.nx];
+  for (int m = 0; m < E; ++m) v[0][m] = col[t * a.nx + m * rs];
   block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);
   // K(dt) = a_j(kx) b(ky) / (nx ny) as z + (K' - 1) z, K' - 1 = (a-1)(b-1) + (a-1) + (b-1);
   // the exact power of two 1/(nx ny) is applied last.
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
   }
   block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
 #pragma unroll
-  for (int m = 0; m < E; ++m) col[(long)(t + m * TT) * a.nx] = v[0][m];
+  for (int m = 0; m < E; ++m) col[t * a.nx + m * rs] = v[0][m];
 }
 
 // --------------------------------------------------------- energy passes
@@ -329,7 +334,7 @@ __device__ __forceinline__ int kbin(int i, int n) { return i < n / 2 ? i : i - n
 // Real-space energy densities (trap, detuning, Raman, interaction, atom
 // numbers) in FP64, then the forward x-FFT of both components into scratch.
 template <class T, int LOGN, int LOGE>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? kRowMaxThreads : 2 * kRowMaxThreads) energy_row(const EnergyArgs a) {
+__global__ void __launch_bounds__(2 * kRowMaxThreads) energy_row(const EnergyArgs a) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);

@@ -7,19 +7,22 @@
 
 namespace spgpe {
 
-// Elements per thread of the row pass: 16 complex64 or 8 complex128 values
-// per component (both components live in the same thread).
-template <class T> constexpr int row_loge(int logn) { return std::min(logn, sizeof(T) == 4 ? 4 : 3); }
+// Elements per thread of the row pass (one component per thread): 16
+// complex64 or 8 complex128 values, 16 complex128 at nx = 4096 so that one
+// row fits a 512-thread block.
+template <class T> constexpr int row_loge(int logn) {
+  return sizeof(T) == 4 ? std::min(logn, 4) : (logn >= 12 ? 4 : std::min(logn, 3));
+}
 
 template <class T> LaunchShape row_shape(int nx, int ny) {
   int logn = 0;
   while ((1 << logn) < nx) ++logn;
   const int E = 1 << row_loge<T>(logn);
-  const int TT = nx / E;
-  const int rows = std::max(1, std::min(kRowMaxThreads / TT, ny));
+  const int TT = nx / E;  // threads per component of a row
+  const int rows = std::max(1, std::min(kRowMaxThreads / (2 * TT), ny));
   LaunchShape s;
   s.elems_per_thread = E;
-  s.threads = rows * TT;
+  s.threads = 2 * rows * TT;
   s.blocks_x = ny / rows;
   s.rows_or_cols = rows;
   s.smem = (size_t)rows * row_stride(nx, sizeof(cx<T>)) * sizeof(cx<T>);
