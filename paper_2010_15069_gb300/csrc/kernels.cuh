@@ -60,20 +60,24 @@ template <bool IMAG, class T> __device__ __forceinline__ void rot_compose(T &m, 
 
 // X: (u, d) <- exp(-i theta sigma_x) (u, d) with (m, s) = (cos theta - 1, sin theta);
 // imaginary time exp(-theta sigma_x) with (cosh theta - 1, sinh theta).
+// Each output is a + (m a + s b'): the small terms are summed first and the
+// large one added last, so the second-order term m a (often below half an
+// ulp of a) is not rounded away.  Dropping it would leave |X|^2 = 1 + s^2 and
+// grow the atom number by s^2 at every application.
 template <bool IMAG, class T> __device__ __forceinline__ void opX(cx<T> &u, cx<T> &d, T m, T s) {
   const cx<T> a = u, b = d;
   if constexpr (IMAG) {
-    u = {d_fma(m, a.re, d_fma(-s, b.re, a.re)), d_fma(m, a.im, d_fma(-s, b.im, a.im))};
-    d = {d_fma(m, b.re, d_fma(-s, a.re, b.re)), d_fma(m, b.im, d_fma(-s, a.im, b.im))};
+    u = {a.re + d_fma(m, a.re, -s * b.re), a.im + d_fma(m, a.im, -s * b.im)};
+    d = {b.re + d_fma(m, b.re, -s * a.re), b.im + d_fma(m, b.im, -s * a.im)};
   } else {
-    u = {d_fma(m, a.re, d_fma(s, b.im, a.re)), d_fma(m, a.im, d_fma(-s, b.re, a.im))};
-    d = {d_fma(m, b.re, d_fma(s, a.im, b.re)), d_fma(m, b.im, d_fma(-s, a.re, b.im))};
+    u = {a.re + d_fma(m, a.re, s * b.im), a.im + d_fma(m, a.im, -s * b.re)};
+    d = {b.re + d_fma(m, b.re, s * a.im), b.im + d_fma(m, b.im, -s * a.re)};
   }
 }
 
-// z <- z + z w for a complex w = f - 1.
+// z <- z + z w for a complex w = f - 1 (small part first, as in opX).
 template <class T> __device__ __forceinline__ cx<T> add_mul1(cx<T> z, cx<T> w) {
-  return {d_fma(z.re, w.re, d_fma(-z.im, w.im, z.re)), d_fma(z.re, w.im, d_fma(z.im, w.re, z.im))};
+  return {z.re + d_fma(z.re, w.re, -(z.im * w.im)), z.im + d_fma(z.re, w.im, z.im * w.re)};
 }
 
 // D(tau): diagonal potential + mean-field phase (decay), densities on entry.
