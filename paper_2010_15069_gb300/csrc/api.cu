@@ -129,33 +129,24 @@ void free_all(spgpe_ctx *c) {
   if (c->plan_ok) cufftDestroy(c->plan);
 }
 
-// Forward roots exp(-2 pi i m / n) in single precision.  Of the nine float
-// pairs within one ulp of the rounded (cos, sin), take the one whose squared
-// modulus is closest to one (evaluated exactly in double): the transforms use
-// each root at every step, so a modulus error that always has the same sign
-// would scale the spinor by a fixed factor per step.
+// Forward roots exp(-2 pi i m / n) for the single-precision transforms, as
+// (tan(phi/2), sin(phi), g, 0) with exp(-2 pi i m / n) = g exp(i phi),
+// g = +-1, phi in [-pi/2, pi/2]; the kernels rotate by phi with three shears
+// (determinant one whatever the rounding) and multiply by g exactly.
 std::vector<float> roots_f32(int n) {
-  std::vector<float> w(2 * (size_t)n);
+  std::vector<float> w(4 * (size_t)n);
   for (int m = 0; m < n; ++m) {
-    const double c = std::cos(kTwoPi * m / n), s = -std::sin(kTwoPi * m / n);
-    const float cf = (float)c, sf = (float)s;
-    float best_c = cf, best_s = sf;
-    double best = 1e300, best_ph = 1e300;
-    for (int i = -1; i <= 1; ++i)
-      for (int j = -1; j <= 1; ++j) {
-        const float cc = i < 0 ? std::nextafter(cf, -2.0f) : i > 0 ? std::nextafter(cf, 2.0f) : cf;
-        const float ss = j < 0 ? std::nextafter(sf, -2.0f) : j > 0 ? std::nextafter(sf, 2.0f) : sf;
-        const double mod = std::fabs((double)cc * cc + (double)ss * ss - 1.0);
-        const double ph = std::fabs((double)cc - c) + std::fabs((double)ss - s);
-        if (mod < best || (mod == best && ph < best_ph)) {
-          best = mod;
-          best_ph = ph;
-          best_c = cc;
-          best_s = ss;
-        }
-      }
-    w[2 * m] = best_c;
-    w[2 * m + 1] = best_s;
+    double th = -kTwoPi * m / n;                 // (-2 pi, 0]
+    if (th <= -0.5 * kTwoPi) th += kTwoPi;       // (-pi, pi]
+    double g = 1.0, phi = th;
+    if (std::fabs(th) > 0.25 * kTwoPi) {         // left half plane: rotate by th -+ pi, negate
+      g = -1.0;
+      phi = th > 0 ? th - 0.5 * kTwoPi : th + 0.5 * kTwoPi;
+    }
+    w[4 * m] = (float)std::tan(0.5 * phi);
+    w[4 * m + 1] = (float)std::sin(phi);
+    w[4 * m + 2] = (float)g;
+    w[4 * m + 3] = 0.0f;
   }
   return w;
 }
@@ -427,7 +418,7 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
   // (6 per row block + 2 per column block), norms (256 blocks of 2)
   c->n_partials = (size_t)ninst * (6 * (size_t)ny + 2 * (size_t)nx + 2 * 1024);
   int r;
-  if ((r = dev_alloc(c, &c->d_twx, nx * es)) || (r = dev_alloc(c, &c->d_twy, ny * es)) ||
+  if ((r = dev_alloc(c, &c->d_twx, (size_t)nx * 16)) || (r = dev_alloc(c, &c->d_twy, (size_t)ny * 16)) ||
       (r = dev_alloc(c, &c->d_tabx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_taby, (size_t)ninst * ny * q)) ||
       (r = dev_alloc(c, &c->d_rawx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_rawy, (size_t)ninst * ny * q)) ||
       (r = dev_alloc(c, &c->d_kxt, (size_t)ninst * 2 * nx * es)) || (r = dev_alloc(c, &c->d_kyt, ny * es)) ||

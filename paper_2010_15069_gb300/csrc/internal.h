@@ -29,7 +29,7 @@ struct RowArgs {
   const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, cos-1, sin} step table
   const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, cos-1, sin} step table
   const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
-  const void *tw;         // [nx] forward roots exp(-2 pi i m / nx)
+  const void *tw;         // [nx] forward roots (see TwType in fft_core.cuh)
   const double *gpar;     // [ninst][4] {g11, g22, g12, kL}
   double tau;             // D substep (dt/2)
   double xang;            // X(dt/4) rotation angle per unit Omega (dt/8)
@@ -48,7 +48,7 @@ struct ColArgs {
   void *psi;
   const void *kxt;        // [ninst][2][nx] complex a_j(kx) - 1
   const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
-  const void *tw;         // [ny] forward roots
+  const void *tw;         // [ny] forward roots (see TwType in fft_core.cuh)
   int nx, ny, ninst, C;
 };
 

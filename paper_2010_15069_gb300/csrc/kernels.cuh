@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass(const RowArgs a) 
   const int inst = blockIdx.y;
   const int y = blockIdx.x * a.rows + lrow;
   cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N;
-  const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+  const void *tw = a.tw;
   constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
   const RowAcc<T> acc{sm + lrow * row_stride(N, sizeof(cx<T>)) + comp * PADN, 0};
 
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
   const int comp = blockIdx.y, inst = blockIdx.z;
   const int kx = blockIdx.x * C + c;
   cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + ((long)inst * 2 + comp) * (long)N * a.nx + kx;
-  const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw);
+  const void *tw = a.tw;
   const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
   const int rs = TT * a.nx;  // element offset between a thread's rows (fits in 32 bits)
 
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) energy_row(const EnergyArg
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < 6; ++k) a.partials[((long)inst * gridDim.x + blockIdx.x) * 6 + k] = acc6[k];
-  block_fft<LOGN, LOGE, -1, 2>(v, t, reinterpret_cast<const cx<T> *>(a.twx), acc);
+  block_fft<LOGN, LOGE, -1, 2>(v, t, a.twx, acc);
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     oup[t + m * TT] = v[0][m];
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(512) energy_col(const EnergyArgs a) {
   cx<T> v[1][E];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[0][m] = col[(long)(t + m * TT) * a.nx];
-  block_fft<LOGN, LOGE, -1, 1>(v, t, reinterpret_cast<const cx<T> *>(a.twy), acc);
+  block_fft<LOGN, LOGE, -1, 1>(v, t, a.twy, acc);
   const double kL = a.gpar[4 * inst + 3];
   const double kx = a.dkx * kbin(ix, a.nx);
   const double shift = (comp == 0 ? -kL : kL) * kx;
