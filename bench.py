@@ -156,6 +156,38 @@ def oracle_rate(budget_s=12.0, max_steps=400):
     return NX * NY * n / dt, n, dt
 
 
+KERNEL_SOURCES = ["fft_core.cuh", "kernels.cuh", "fastmath.cuh", "internal.h", "launch_row.cuh",
+                  "launch_col.cuh", "api.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_15069_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(key):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, or
+    None when no summary covers this kernel or the kernel sources changed since
+    the counters were taken (summaries record the hash of the sources)."""
+    import glob
+    cur = kernel_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            lines = f.read().splitlines()
+        srcs = [ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("kernel-sources:")]
+        if not srcs or srcs[0] != cur:
+            continue
+        for ln in lines:
+            parts = ln.split()
+            if len(parts) == 3 and parts[0] == "traffic_bytes_per_launch" and parts[1] == key:
+                return int(parts[2])
+    return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -256,14 +288,7 @@ def run_fused(args):
     alg_bytes = BYTES_PER_PT_PASS[dtype] * pts
     peak, peak_kind = peaks()
     achieved = alg_bytes / avg_s / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                traffic = json.load(f).get(f"{dom}:{dtype}:{B}")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = measured_traffic(f"{dom}:{dtype}:{B}")
 
     # end to end through the C ABI with pinned host buffers: H2D, one step, D2H
     host = torch.empty(tuple(t.shape), dtype=t.dtype, pin_memory=True)
