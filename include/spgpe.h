@@ -162,6 +162,28 @@ int spgpe_last_launches(const spgpe_ctx *ctx);
 int spgpe_set_timing(spgpe_ctx *ctx, int enable);
 int spgpe_timing(spgpe_ctx *ctx, double *ms_out, int *count_out);
 
+/* Atom numbers of a spinor batch without allocating any memory (the paper has
+ * no counterpart: this serves callers that cannot call cudaMalloc, such as
+ * host applications or plugins that hand out all device memory from their own
+ * pool, or that run under a fixed device-memory budget where a library may not
+ * allocate).  No context is needed and nothing is allocated, on the device or
+ * the host: the partial sums live in a 256 KiB array of device memory that is
+ * part of the library and that every GPU loading it keeps until the process
+ * exits.  psi is the caller's device buffer [ninst][2][ny][nx] complex of the
+ * given dtype (SPGPE_C64 or SPGPE_C128) over [-xmax, xmax) x [-ymax, ymax);
+ * out is a host array of 2*ninst doubles receiving {N_up, N_dn} per instance
+ * (dx dy sum |psi_j|^2, FP64 accumulation).  Runs on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream) and synchronises it.
+ * The first call on a device looks up the device address of the array, so
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (from several streams or threads) race
+ * and must be serialised by the caller.  Returns EINVAL for NULL pointers,
+ * sizes below one, nx*ny above 2^30, a bad dtype or extent, or ninst above
+ * 252 (the capacity of the array); ECUDA when a CUDA call fails; ENONFINITE if
+ * a sum is not finite. */
+int spgpe_norm_noalloc(const void *psi, int nx, int ny, int ninst, double xmax,
+                       double ymax, int dtype, void *cuda_stream, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,7 @@ SIGNATURES = {
     "spgpe_last_launches": (_I, [_P]),
     "spgpe_set_timing": (_I, [_P, _I]),
     "spgpe_timing": (_I, [_P, _P, _P]),
+    "spgpe_norm_noalloc": (_I, [_P, _I, _I, _I, _D, _D, _I, _P, _P]),
 }
 NKINDS = 9
 KIND_NAMES = ["row_real_open", "row_real_fused", "row_real_close", "col_real", "row_imag_open",
