@@ -1,14 +1,18 @@
 // C ABI of the fused TSSP solver (include/spgpe.h): context, operator tables,
 // step scheduling, reductions, and the cuFFT comparator.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cufft.h>
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
-#include "../../include/spgpe.h"
+#include "spgpe.h"
 #include "internal.h"
 
 using namespace spgpe;
@@ -51,9 +55,20 @@ struct spgpe_ctx {
   void *d_stage = nullptr;    // psi-sized: staging of host spinors
   double tab_dt = NAN;
   int tab_imag = -1;
+  int omega_pieces = 0;
+  double vbound2d = 0.0;  // max |V +- delta/2| of the 2D arrays (0 when separable)
 
   cufftHandle plan = 0;
   bool plan_ok = false;
+
+  // Persistent passes: multiprocessor count, and the column tensor map of the
+  // spinor buffer last stepped (rebuilt when the buffer changes).
+  int sms = 0;
+  bool persistent_row = false;  // the row pass is arithmetic-bound: the plain pass is faster
+  bool persistent_col = true;
+  const void *map_psi = nullptr;
+  CUtensorMap map{};
+  void *d_gparT = nullptr;
 
   std::string err;
   int last_launches = 0;
@@ -116,6 +131,7 @@ int dev_alloc(spgpe_ctx *c, void **p, size_t bytes) {
 }
 
 void free_all(spgpe_ctx *c) {
+  if (c->d_gparT) cudaFree(c->d_gparT);
   for (auto &u : c->ev_used) {
     cudaEventDestroy(u.second.first);
     cudaEventDestroy(u.second.second);
@@ -130,11 +146,12 @@ void free_all(spgpe_ctx *c) {
 }
 
 // Forward roots exp(-2 pi i m / n) for the single-precision transforms, as
-// (tan(phi/2), sin(phi), g, 0) with exp(-2 pi i m / n) = g exp(i phi),
-// g = +-1, phi in [-pi/2, pi/2]; the kernels rotate by phi with three shears
-// (determinant one whatever the rounding) and multiply by g exactly.
+// (tan(phi/2), sin(phi)) with exp(-2 pi i m / n) = g exp(i phi), g = +-1,
+// phi in [-pi/2, pi/2]; the kernels rotate by phi with three shears
+// (determinant one whatever the rounding) and negate exactly where g = -1
+// (n/4 < m < 3n/4, recomputed from m).
 std::vector<float> roots_f32(int n) {
-  std::vector<float> w(4 * (size_t)n);
+  std::vector<float> w(2 * (size_t)n);
   for (int m = 0; m < n; ++m) {
     double th = -kTwoPi * m / n;                 // (-2 pi, 0]
     if (th <= -0.5 * kTwoPi) th += kTwoPi;       // (-pi, pi]
@@ -143,10 +160,9 @@ std::vector<float> roots_f32(int n) {
       g = -1.0;
       phi = th > 0 ? th - 0.5 * kTwoPi : th + 0.5 * kTwoPi;
     }
-    w[4 * m] = (float)std::tan(0.5 * phi);
-    w[4 * m + 1] = (float)std::sin(phi);
-    w[4 * m + 2] = (float)g;
-    w[4 * m + 3] = 0.0f;
+    (void)g;
+    w[2 * m] = (float)std::tan(0.5 * phi);
+    w[2 * m + 1] = (float)std::sin(phi);
   }
   return w;
 }
@@ -177,16 +193,43 @@ int upload_raw(spgpe_ctx *c) {
   r = upload(c, c->d_rawy, ry);
   if (r) return r;
   CK(c, cudaMemcpyAsync(c->d_gpar, c->hg.data(), c->hg.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  // Working-precision couplings {g11, g22, g12, Vb}, Vb = max |V +- delta/2| of
+  // the instance: the kernels bound the D phase with it to pick the small-phase
+  // series for a whole warp.
+  std::vector<double> gt(c->hg.size());
+  for (int i = 0; i < c->ninst; ++i) {
+    double vb = 0.0;
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+      for (int x = 0; x < c->nx; ++x) {
+        const double *h = &c->hx[((size_t)i * c->nx + x) * 3];
+        const double v = h[0] + 0.5 * sgn * h[1];
+        xmin = std::min(xmin, v);
+        xmax = std::max(xmax, v);
+      }
+      for (int y = 0; y < c->ny; ++y) {
+        const double *h = &c->hy[((size_t)i * c->ny + y) * 3];
+        const double v = h[0] + 0.5 * sgn * h[1];
+        ymin = std::min(ymin, v);
+        ymax = std::max(ymax, v);
+      }
+      vb = std::max(vb, std::max(std::fabs(xmin + ymin), std::fabs(xmax + ymax)));
+    }
+    gt[4 * i] = c->hg[4 * i];
+    gt[4 * i + 1] = c->hg[4 * i + 1];
+    gt[4 * i + 2] = c->hg[4 * i + 2];
+    gt[4 * i + 3] = vb + c->vbound2d;
+  }
+  if ((r = upload(c, c->d_gparT, gt))) return r;
   c->tab_dt = NAN;  // step tables depend on the model
   return SPGPE_OK;
 }
 
-// Step tables for substep dt (real or imaginary time).  Unit-modulus factors
-// are stored as (f - 1) to full relative precision (the kernels apply
-// z + (f - 1) z):
-//   x/y step tables {V + delta/2, V - delta/2, m, s} of the separable pieces,
-//   (m, s) = (cos a - 1, sin a) or (cosh a - 1, sinh a), a = Omega_piece dt / 8
-//   (the angle of X(dt/4));
+// Step tables for substep dt (real or imaginary time):
+//   x/y step tables {V + delta/2, V - delta/2, X constants} of the separable
+//   pieces, X constants for the angle a = Omega_piece dt / 8 of X(dt/4):
+//   (tan(a/2), sin a) in real time (three-shear rotation), (cosh a - 1,
+//   sinh a) in imaginary time (to full relative precision);
 //   K tables a_j(kx) - 1 with a_j = exp(-i dt (kx^2/2 -+ kL kx)) and b(ky) - 1
 //   with b = exp(-i dt ky^2/2) (imaginary time: exp(-dt (...)) - 1); the
 //   1/(nx ny) of the inverse transform is applied in the kernel.
@@ -194,14 +237,15 @@ int ensure_tables(spgpe_ctx *c, double dt, int imag) {
   if (c->tab_dt == dt && c->tab_imag == imag) return SPGPE_OK;
   const int nx = c->nx, ny = c->ny, ni = c->ninst;
   std::vector<double> tx((size_t)ni * nx * 4), ty((size_t)ni * ny * 4);
+  bool too_big = false;
   auto rot = [&](double ang, double &mm, double &ss) {
     if (imag) {
       const double sh = std::sinh(0.5 * ang);
       mm = 2.0 * sh * sh;
       ss = std::sinh(ang);
     } else {
-      const double sh = std::sin(0.5 * ang);
-      mm = -2.0 * sh * sh;
+      if (std::fabs(ang) > 0.25 * kTwoPi) too_big = true;
+      mm = std::tan(0.5 * ang);
       ss = std::sin(ang);
     }
   };
@@ -245,6 +289,14 @@ int ensure_tables(spgpe_ctx *c, double dt, int imag) {
     const double k = kval(y, ny, c->dy);
     em1(dt * 0.5 * k * k, &ky[2 * (size_t)y]);
   }
+  if (too_big) return fail(c, SPGPE_EINVAL, "|Omega| dt / 8 exceeds pi/2: time step too large for the Raman coupling");
+  c->omega_pieces = 0;
+  for (int i = 0; i < ni; ++i) {
+    for (int y = 0; y < ny; ++y)
+      if (c->hy[((size_t)i * ny + y) * 3 + 2] != 0.0) c->omega_pieces |= 1;
+    for (int x = 0; x < nx; ++x)
+      if (c->hx[((size_t)i * nx + x) * 3 + 2] != 0.0) c->omega_pieces |= 2;
+  }
   int r;
   if ((r = upload(c, c->d_tabx, tx)) || (r = upload(c, c->d_taby, ty)) || (r = upload(c, c->d_kxt, kx)) ||
       (r = upload(c, c->d_kyt, ky)))
@@ -271,8 +323,13 @@ RowArgs row_args(spgpe_ctx *c, void *psi, double dt) {
   a.pot2d = c->has2d ? c->d_pot2d : nullptr;
   a.tw = c->d_twx;
   a.gpar = c->d_gpar;
+  a.gparT = c->d_gparT;
   a.tau = 0.5 * dt;
   a.xang = dt / 8.0;
+  a.htau_d = c->tab_imag ? -a.tau : -0.5 * a.tau;
+  a.htau_f = (float)a.htau_d;
+  a.xang_f = (float)a.xang;
+  a.omega_pieces = c->omega_pieces;
   a.partials = c->d_partials;
   a.counters = c->d_counters;
   a.scale = c->d_scale;
@@ -293,6 +350,9 @@ ColArgs col_args(spgpe_ctx *c, void *psi) {
   a.kxt = c->d_kxt;
   a.kyt = c->d_kyt;
   a.tw = c->d_twy;
+  a.inv_d = 1.0 / ((double)c->nx * c->ny);
+  a.inv_f = (float)a.inv_d;
+  a.flags = c->d_flags;
   a.nx = c->nx;
   a.ny = c->ny;
   a.ninst = c->ninst;
@@ -336,14 +396,57 @@ template <class F> cudaError_t timed(spgpe_ctx *c, int kind, F &&launch) {
   return e;
 }
 
+bool aligned16(const void *psi) { return (reinterpret_cast<uintptr_t>(psi) & 15) == 0; }
+
 cudaError_t row(spgpe_ctx *c, int flags, const RowArgs &a) {
+  const bool p = c->persistent_row && c->sms > 0 && aligned16(a.psi);
   return timed(c, kind_of_row(flags), [&] {
+    if (p) {
+      const cudaError_t e = c->dtype == SPGPE_C64 ? launch_row_p<float>(flags, a, c->st, c->sms)
+                                                  : launch_row_p<double>(flags, a, c->st, c->sms);
+      if (e != cudaErrorNotSupported) return e;
+    }
     return c->dtype == SPGPE_C64 ? launch_row<float>(flags, a, c->st) : launch_row<double>(flags, a, c->st);
   });
 }
 
+// Tensor map over the spinor buffer viewed as [ninst*2*ny rows][nx complex]
+// (8-byte elements: one complex64, or half a complex128), with a box of C
+// complex columns by min(ny, 256) rows.
+cudaError_t ensure_map(spgpe_ctx *c, const void *psi) {
+  if (c->map_psi == psi) return cudaSuccess;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int xm = c->dtype == SPGPE_C64 ? 1 : 2;
+  const int C = c->dtype == SPGPE_C64 ? colp_cols<float>(c->nx, c->ny) : colp_cols<double>(c->nx, c->ny);
+  const cuuint64_t dims[2] = {(cuuint64_t)c->nx * xm, (cuuint64_t)c->ninst * 2 * c->ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)c->nx * c->es};
+  const cuuint32_t box[2] = {(cuuint32_t)(C * xm), (cuuint32_t)std::min(c->ny, 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&c->map, c->dtype == SPGPE_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                            2, const_cast<void *>(psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  c->map_psi = psi;
+  return cudaSuccess;
+}
+
 cudaError_t col(spgpe_ctx *c, bool imag, const ColArgs &a) {
+  bool p = c->persistent_col && c->sms > 0 && aligned16(a.psi);
+  if (p && ensure_map(c, a.psi) != cudaSuccess) p = false;
   return timed(c, imag ? 8 : 3, [&] {
+    if (p) {
+      const cudaError_t e = c->dtype == SPGPE_C64 ? launch_col_p<float>(imag, a, c->map, c->st, c->sms)
+                                                  : launch_col_p<double>(imag, a, c->map, c->st, c->sms);
+      if (e != cudaErrorNotSupported) return e;
+    }
     return c->dtype == SPGPE_C64 ? launch_col<float>(imag, a, c->st) : launch_col<double>(imag, a, c->st);
   });
 }
@@ -383,6 +486,7 @@ int read_flags(spgpe_ctx *c) {
   CK(c, cudaStreamSynchronize(c->st));
   if (h) {
     CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->st));
+    if (h & 2) return fail(c, SPGPE_ETIMEOUT, "a tile transfer did not complete within the wait limit");
     return fail(c, SPGPE_ENONFINITE, "non-finite or zero atom number met during imaginary-time renormalisation");
   }
   return SPGPE_OK;
@@ -423,6 +527,7 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
       (r = dev_alloc(c, &c->d_rawx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_rawy, (size_t)ninst * ny * q)) ||
       (r = dev_alloc(c, &c->d_kxt, (size_t)ninst * 2 * nx * es)) || (r = dev_alloc(c, &c->d_kyt, ny * es)) ||
       (r = dev_alloc(c, (void **)&c->d_gpar, (size_t)ninst * 4 * sizeof(double))) ||
+      (r = dev_alloc(c, &c->d_gparT, (size_t)ninst * 4 * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_partials, c->n_partials * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_counters, (size_t)ninst * sizeof(unsigned))) ||
       (r = dev_alloc(c, (void **)&c->d_scale, (size_t)ninst * 2 * sizeof(double))) ||
@@ -439,6 +544,19 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
     free_all(c);
     delete c;
     return SPGPE_ECUDA;
+  }
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      c->sms = 0;
+    cudaGetLastError();
+    // SPGPE_PERSISTENT selects the pass variants: 0 plain passes, 1 persistent
+    // column pass (default), 2 persistent row and column passes.
+    const char *env = std::getenv("SPGPE_PERSISTENT");
+    if (env && env[0] >= '0' && env[0] <= '2') {
+      c->persistent_col = env[0] != '0';
+      c->persistent_row = env[0] == '2';
+    }
   }
   if (dtype == SPGPE_C64) {
     const std::vector<float> wx = roots_f32(nx), wy = roots_f32(ny);
@@ -499,12 +617,14 @@ int spgpe_set_potentials(spgpe_ctx *c, const double *V, const double *delta, con
   for (int i = 0; i < c->ninst; ++i)
     for (int k = 0; k < 4; ++k) c->hg[4 * i + k] = g[k];
   std::vector<double> p2(n * 4);
+  c->vbound2d = 0.0;
   for (size_t i = 0; i < n; ++i) {
     const double v = V ? V[i] : 0.0, d = delta ? delta[i] : 0.0, o = Omega ? Omega[i] : 0.0;
     p2[4 * i] = v + 0.5 * d;
     p2[4 * i + 1] = v - 0.5 * d;
     p2[4 * i + 2] = o;
     p2[4 * i + 3] = 0.0;
+    c->vbound2d = std::max(c->vbound2d, std::max(std::fabs(p2[4 * i]), std::fabs(p2[4 * i + 1])));
   }
   int r = dev_alloc(c, &c->d_pot2d, n * 2 * c->es);
   if (r) return r;
@@ -530,6 +650,7 @@ int spgpe_set_potentials_separable(spgpe_ctx *c, int inst, const double *Vx, con
   if (c->has2d) {
     // a separable call replaces the 2D model for every instance
     c->has2d = false;
+    c->vbound2d = 0.0;
     if (inst >= 0) std::fill(c->inst_set.begin(), c->inst_set.end(), 0);
   }
   const int i0 = inst < 0 ? 0 : inst, i1 = inst < 0 ? c->ninst : inst + 1;
@@ -572,7 +693,8 @@ int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
     CK(c, col(c, false, ca));
     CK(c, row(c, s < nsteps ? kRealMid : kRealLast, ra));
   }
-  return end_psi(c, psi, host);
+  if ((r = end_psi(c, psi, host))) return r;
+  return host ? read_flags(c) : SPGPE_OK;
 }
 
 int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_mode, const double *target,

@@ -28,6 +28,17 @@ constexpr float kTwoOverPi = 0.63661977236758134308f;
 // exp(2ir) - 1 = -2 sin^2 r + 2i sin r cos r, sin r and cos r from their
 // Taylor series (truncation below 2e-9 at |r| = pi/4).
 __device__ __forceinline__ void expi2_m1(float h, float &wre, float &wim) {
+  if (fabsf(h) < 0.125f) {
+    // Small half phases (the usual case for a stable time step): the series of
+    // exp(2ih) - 1 directly, truncation below 1e-12 relative for |h| < 1/8:
+    // cos 2h - 1 = -2h^2 + 2h^4/3 - 4h^6/45 + 2h^8/315,
+    // sin 2h = 2h - 4h^3/3 + 4h^5/15 - 8h^7/315 + 4h^9/2835.
+    const float h2 = h * h;
+    wre = h2 * fmaf(h2, fmaf(h2, fmaf(h2, 6.3492063492e-3f, -8.8888888889e-2f), 0.66666666667f), -2.0f);
+    wim = h * fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 1.4109347443e-3f, -2.5396825397e-2f), 0.26666666667f),
+                            -1.3333333333f), 2.0f);
+    return;
+  }
   const int n = __float2int_rn(h * kTwoOverPi);
   const float fn = (float)n;
   float r = fmaf(-fn, kPio2A, h);
@@ -54,6 +65,81 @@ __device__ __forceinline__ void expi2_m1(float h, float &wre, float &wim) {
   wim = b;
 }
 
+// Shear constants of a rotation by 2h: t = tan(h), s = sin(2h); neg is set
+// when the rotation is by 2r + pi with |r| <= pi/4 (apply R(2r), then negate).
+// Series for small |h| (three tiers: |h| < 1/32, < 1/8, else reduced), so the
+// common case of a small phase costs a handful of fma:
+// tan h = h + h^3/3 + 2h^5/15 + 17h^7/315 + 62h^9/2835 + ...,
+// sin 2h = 2h - 4h^3/3 + 4h^5/15 - 8h^7/315 + 4h^9/2835 - ...
+__device__ __forceinline__ void shear_consts_2h(float h, float &t, float &s, bool &neg) {
+  const float ah = fabsf(h);
+  neg = false;
+  if (ah < 0.03125f) {  // truncation below 2e-11 relative
+    const float h2 = h * h;
+    t = h * fmaf(h2, fmaf(h2, 0.13333333333f, 0.33333333333f), 1.0f);
+    s = h * fmaf(h2, fmaf(h2, 0.26666666667f, -1.3333333333f), 2.0f);
+  } else if (ah < 0.125f) {  // truncation below 1e-12 relative
+    const float h2 = h * h;
+    t = h * fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 2.1869488536e-2f, 5.3968253968e-2f), 0.13333333333f),
+                      0.33333333333f), 1.0f);
+    s = h * fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 1.4109347443e-3f, -2.5396825397e-2f), 0.26666666667f),
+                      -1.3333333333f), 2.0f);
+  } else {
+    const int n = __float2int_rn(h * kTwoOverPi);
+    const float fn = (float)n;
+    float r = fmaf(-fn, kPio2A, h);
+    r = fmaf(-fn, kPio2B, r);
+    r = fmaf(-fn, kPio2C, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.7557319224e-6f, -1.9841269841e-4f);
+    ps = fmaf(r2, ps, 8.3333333333e-3f);
+    ps = fmaf(r2, ps, -1.6666666667e-1f);
+    const float sr = fmaf(r * r2, ps, r);
+    float pc = fmaf(r2, -2.7557319224e-7f, 2.4801587302e-5f);
+    pc = fmaf(r2, pc, -1.3888888889e-3f);
+    pc = fmaf(r2, pc, 4.1666666667e-2f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cr = fmaf(r2, pc, 1.0f);
+    t = sr / cr;
+    s = 2.0f * sr * cr;
+    neg = (n & 1) != 0;  // exp(2ih) = -exp(2ir)
+  }
+}
+
+// The middle tier alone, for callers that know |h| < 1/8 for a whole warp.
+__device__ __forceinline__ void shear_consts_2h_small(float h, float &t, float &s) {
+  const float h2 = h * h;
+  t = h * fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 2.1869488536e-2f, 5.3968253968e-2f), 0.13333333333f),
+                    0.33333333333f), 1.0f);
+  s = h * fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 1.4109347443e-3f, -2.5396825397e-2f), 0.26666666667f),
+                    -1.3333333333f), 2.0f);
+}
+
+// Double precision: the CUDA math library.
+__device__ __forceinline__ void shear_consts_2h(double h, double &t, double &s, bool &neg) {
+  double sh, ch;
+  sincos(h, &sh, &ch);
+  const double a = fabs(h);
+  neg = false;
+  if (a <= 0.78539816339744830962) {
+    t = sh / ch;
+    s = 2.0 * sh * ch;
+  } else {
+    // rotate by 2h - pi (|h - pi/2| < pi/2 folded to |r| <= pi/4) and negate
+    const double n = rint(h * 0.63661977236758134308);
+    const double r = h - n * 1.57079632679489661923;
+    double sr, cr;
+    sincos(r, &sr, &cr);
+    t = sr / cr;
+    s = 2.0 * sr * cr;
+    neg = (((long long)n) & 1) != 0;
+  }
+}
+__device__ __forceinline__ void shear_consts_2h_small(double h, double &t, double &s) {
+  bool neg;
+  shear_consts_2h(h, t, s, neg);
+}
+
 // ln 2 = A + B, A with 12 significant bits (k * A exact for |k| < 2^12).
 constexpr float kLn2A = 0.693115234375f;             // 0x3F317000
 constexpr float kLn2B = 3.1946183299e-05f;
@@ -64,6 +150,15 @@ constexpr float kInvLn2 = 1.4426950408889634074f;
 // expm1(x) = 2^k expm1(r) + (2^k - 1).  Saturates to -1 below x = -87 and to
 // about 1.7e38 above 88.
 __device__ __forceinline__ float expm1_f(float x) {
+  if (fabsf(x) < 0.0625f) {
+    // small arguments: x + x^2/2! + ... + x^7/7! (truncation below 1e-13 relative)
+    float p = fmaf(x, 1.9841269841e-4f, 1.3888888889e-3f);
+    p = fmaf(x, p, 8.3333333333e-3f);
+    p = fmaf(x, p, 4.1666666667e-2f);
+    p = fmaf(x, p, 1.6666666667e-1f);
+    p = fmaf(x, p, 0.5f);
+    return fmaf(x * x, p, x);
+  }
   x = fminf(fmaxf(x, -87.0f), 88.0f);
   const int k = __float2int_rn(x * kInvLn2);
   const float fk = (float)k;
@@ -82,7 +177,23 @@ __device__ __forceinline__ float expm1_f(float x) {
   return fmaf(s, em, s - 1.0f);
 }
 
+// expm1 for |x| < 1/2 (callers that know the bound for a whole warp):
+// Taylor series to x^11/11!, truncation below 1e-12 relative.
+__device__ __forceinline__ float expm1_small(float x) {
+  float p = fmaf(x, 2.5052108385e-8f, 2.7557319224e-7f);
+  p = fmaf(x, p, 2.7557319224e-6f);
+  p = fmaf(x, p, 2.4801587302e-5f);
+  p = fmaf(x, p, 1.9841269841e-4f);
+  p = fmaf(x, p, 1.3888888889e-3f);
+  p = fmaf(x, p, 8.3333333333e-3f);
+  p = fmaf(x, p, 4.1666666667e-2f);
+  p = fmaf(x, p, 1.6666666667e-1f);
+  p = fmaf(x, p, 0.5f);
+  return fmaf(x * x, p, x);
+}
+
 // Double precision: the CUDA math library.
+__device__ __forceinline__ double expm1_small(double x) { return expm1(x); }
 __device__ __forceinline__ void expi2_m1(double h, double &wre, double &wim) {
   double s, c;
   sincos(h, &s, &c);

@@ -77,22 +77,24 @@ __device__ __forceinline__ cx<T> w16(cx<T> a) {
 }
 
 // Stage twiddles.  Double precision: the root exp(-2 pi i m / N) as a complex
-// pair.  Single precision: the root as g R(phi), g = +-1 and R(phi) a rotation
-// by phi in [-pi/2, pi/2], stored as (tan(phi/2), sin(phi), g, 0) and applied
-// with three shears.  A single-precision (cos, sin) pair is off unit modulus by
-// about 2^-25 in a direction that does not average out over the set of roots;
-// every element passes through these factors in every transform, and the
-// rounded pairs drained the norm by about 1e-7 per forward/inverse round trip.
+// pair.  Single precision: exp(-2 pi i m / N) = g R(phi) with g = +-1 and
+// R(phi) a rotation by phi in [-pi/2, pi/2], stored as (tan(phi/2), sin(phi))
+// and applied with three shears; g = -1 exactly for N/4 < m < 3N/4 and is
+// recomputed from m.  A single-precision (cos, sin) pair is off unit modulus
+// by about 2^-25 in a direction that does not average out over the set of
+// roots; every element passes through these factors in every transform, and
+// rounded pairs drain the norm by about 1e-7 per forward/inverse round trip.
 template <class T> struct TwType;
-template <> struct TwType<float> { using type = float4; };
+template <> struct TwType<float> { using type = float2; };
 template <> struct TwType<double> { using type = cx<double>; };
 
-template <int SIGN, class T>
-__device__ __forceinline__ cx<T> twiddle(cx<T> u, const typename TwType<T>::type &w) {
+template <int N, int SIGN, class T>
+__device__ __forceinline__ cx<T> twiddle(cx<T> u, const typename TwType<T>::type &w, int m) {
   if constexpr (sizeof(T) == 4) {
     const float t = SIGN < 0 ? w.x : -w.x, s = SIGN < 0 ? w.y : -w.y;  // inverse: R(-phi)
     const cx<T> r = shear_rot(u, t, s);
-    return {w.z * r.re, w.z * r.im};
+    const bool neg = (unsigned)(4 * m - N - 1) < (unsigned)(2 * N - 1);
+    return {neg ? -r.re : r.re, neg ? -r.im : r.im};
   } else {
     const cx<T> c = SIGN < 0 ? w : cx<T>{w.re, -w.im};
     return cmul(u, c);
@@ -169,7 +171,10 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[NSEQ][E], int t,
       for (int r = 0; r < R; ++r) u[r] = v[q][b + r * B];
       if constexpr (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) u[r] = twiddle<SIGN, T>(u[r], tw[(r * k) * (N / (NS * R))]);
+        for (int r = 1; r < R; ++r) {
+          const int m = (r * k) * (N / (NS * R));
+          u[r] = twiddle<N, SIGN, T>(u[r], tw[m], m);
+        }
       }
       dft<R, SIGN>(u);
       if constexpr (LAST) {

@@ -1,5 +1,6 @@
 // Declarations shared by the kernel translation units and the C-ABI layer.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace spgpe {
@@ -26,13 +27,21 @@ constexpr int kImagScale = F_IMAG | F_SCALE;
 // Arguments of the fused row pass (x direction, both components per thread).
 struct RowArgs {
   void *psi;              // [ninst][2][ny][nx] complex, in place
-  const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, cos-1, sin} step table
-  const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, cos-1, sin} step table
+  const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, X constants} step table
+  const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, X constants} step table
+                          // X constants: (tan(a/2), sin a) in real time, (cosh a - 1, sinh a)
+                          // in imaginary time, a = Omega piece * dt / 8
   const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
   const void *tw;         // [nx] forward roots (see TwType in fft_core.cuh)
   const double *gpar;     // [ninst][4] {g11, g22, g12, kL}
+  const void *gparT;      // the same in the working precision
   double tau;             // D substep (dt/2)
   double xang;            // X(dt/4) rotation angle per unit Omega (dt/8)
+  double htau_d;          // -tau/2 (real time, half phase) or -tau (imaginary time)
+  float htau_f;           // the same in single precision
+  float xang_f;           // xang in single precision
+  int tab_in_smem;        // persistent pass: x step table copied with each tile
+  int omega_pieces;       // bit 0: some Omega_y != 0, bit 1: some Omega_x != 0 (separable pieces)
   double *partials;       // [ninst][gridDim.x][2]
   unsigned *counters;     // [ninst], zero between launches
   double *scale;          // [ninst][2]
@@ -46,6 +55,9 @@ struct RowArgs {
 // Arguments of the fused column pass (y direction, one component per block).
 struct ColArgs {
   void *psi;
+  double inv_d;           // 1/(nx ny), an exact power of two
+  float inv_f;
+  int *flags;             // error bits (persistent pass: bit 1 = transfer wait timed out)
   const void *kxt;        // [ninst][2][nx] complex a_j(kx) - 1
   const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
   const void *tw;         // [ny] forward roots (see TwType in fft_core.cuh)
@@ -67,6 +79,7 @@ struct EnergyArgs {
 };
 
 constexpr int kRowMaxThreads = 256;
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per block on GB300
 constexpr int kColMaxThreads = 512;
 
 // Shared-memory element counts (host and device use the same formulas).
@@ -101,6 +114,13 @@ template <class T> cudaError_t launch_norm(const void *psi, long plane, int nins
 template <class T> cudaError_t launch_residual(const void *psi, const void *prev, long plane, int ninst,
                                                double *partials, int blocks, cudaStream_t s);
 template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStream_t s);
+// Persistent passes (async tile loads; psi must be 16-byte aligned).  sms is
+// the device's multiprocessor count; the column pass reads psi through `map`,
+// a 2D tensor map over [ninst*2*ny rows][nx complex] with a box of
+// colp_cols<T>() columns by min(ny, 256) rows.
+template <class T> cudaError_t launch_row_p(int flags, RowArgs a, cudaStream_t s, int sms);
+template <class T> int colp_cols(int nx, int ny);
+template <class T> cudaError_t launch_col_p(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t s, int sms);
 template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t s);
 
 }  // namespace spgpe

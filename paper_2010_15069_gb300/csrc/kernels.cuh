@@ -82,22 +82,106 @@ template <class T> __device__ __forceinline__ cx<T> add_mul1(cx<T> z, cx<T> w) {
 
 // D(tau): diagonal potential + mean-field phase (decay), densities on entry.
 // htau = -tau/2 in real time (the half phase), -tau in imaginary time.
-template <bool IMAG, class T>
+// FAST: the caller has checked, for the whole warp, that |htau e| < 1/8 (real
+// time) or < 1/2 (imaginary time), so the series need no range reduction.
+template <bool IMAG, bool FAST = false, class T>
 __device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T htau) {
   const T ru = d_fma(u.re, u.re, u.im * u.im), rd = d_fma(d.re, d.re, d.im * d.im);
   const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
   const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
-  if constexpr (IMAG) {
+  if constexpr (IMAG && FAST) {
+    const T fu = expm1_small(htau * eu), fd = expm1_small(htau * ed);
+    u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
+    d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
+  } else if constexpr (!IMAG && FAST) {
+    T tu, su, td, sd;
+    shear_consts_2h_small(htau * eu, tu, su);
+    shear_consts_2h_small(htau * ed, td, sd);
+    u = shear_rot(u, tu, su);
+    d = shear_rot(d, td, sd);
+  } else if constexpr (IMAG) {
     const T fu = expm1_f(htau * eu), fd = expm1_f(htau * ed);
     u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
     d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
   } else {
-    cx<T> wu, wd;
-    expi2_m1(htau * eu, wu.re, wu.im);
-    expi2_m1(htau * ed, wd.re, wd.im);
-    u = add_mul1(u, wu);
-    d = add_mul1(d, wd);
+    // the phases exp(-i tau e) as three-shear rotations by 2 h, h = htau e
+    // (determinant one: no systematic change of |psi| from rounded constants)
+    T tu, su, td, sd;
+    bool nu, nd;
+    shear_consts_2h(htau * eu, tu, su, nu);
+    shear_consts_2h(htau * ed, td, sd, nd);
+    u = shear_rot(u, tu, su);
+    d = shear_rot(d, td, sd);
+    if (nu) u = {-u.re, -u.im};
+    if (nd) d = {-d.re, -d.im};
   }
+}
+
+// Real-time X(theta) = exp(-i theta sigma_x) as two independent plane
+// rotations: (Re u, Im d) by -theta and (Im u, Re d) by +theta, each with
+// three shears (t = tan(theta/2), s = sin(theta)); 6 fma, determinant one.
+template <class T> __device__ __forceinline__ void opXr(cx<T> &u, cx<T> &d, T t, T s) {
+  const T x1 = d_fma(t, d.im, u.re);
+  const T y1 = d_fma(-s, x1, d.im);
+  const T x2 = d_fma(t, y1, x1);
+  const T p1 = d_fma(-t, d.re, u.im);
+  const T q1 = d_fma(s, p1, d.re);
+  const T p2 = d_fma(-t, q1, p1);
+  u = {x2, p2};
+  d = {q1, y1};
+}
+
+// X constants at one point.  Imaginary time: (cosh - 1, sinh) of the summed
+// angle.  Real time: the separate rotations of the y piece, the x piece and
+// the 2D piece of the angle (rotations about sigma_x commute), each applied
+// only when that piece is present.
+template <class T> struct XPoint {
+  T m, s;          // imaginary time: composed (cosh - 1, sinh); real time: y piece (tan, sin)
+  T tx, sx;        // real time: x piece
+  T t2, s2;        // real time: 2D piece
+  bool n2;         // 2D piece rotates by 2r + pi: negate afterwards
+};
+
+template <bool IMAG, class T>
+__device__ __forceinline__ void applyX(cx<T> &u, cx<T> &d, const XPoint<T> &x, int pieces) {
+  if constexpr (IMAG) {
+    opX<true>(u, d, x.m, x.s);
+  } else {
+    if (pieces & 1) opXr(u, d, x.m, x.s);
+    if (pieces & 2) opXr(u, d, x.tx, x.sx);
+    if (pieces & 4) {
+      opXr(u, d, x.t2, x.s2);
+      if (x.n2) {
+        u = {-u.re, -u.im};
+        d = {-d.re, -d.im};
+      }
+    }
+  }
+}
+
+// X constants at point (x, y): px, ty are the x and y step-table entries,
+// q2z the 2D Omega (or 0), xang = dt/8.
+template <bool IMAG, class T>
+__device__ __forceinline__ XPoint<T> xpoint(const q4<T> &px, const q4<T> &ty, bool has2d, T q2z, T xang) {
+  XPoint<T> r;
+  if constexpr (IMAG) {
+    r.m = px.z;
+    r.s = px.w;
+    rot_compose<true>(r.m, r.s, ty.z, ty.w);
+    if (has2d) {
+      T m2, s2;
+      rot_of<true>(q2z * xang, m2, s2);
+      rot_compose<true>(r.m, r.s, m2, s2);
+    }
+  } else {
+    r.m = ty.z;
+    r.s = ty.w;
+    r.tx = px.z;
+    r.sx = px.w;
+    r.n2 = false;
+    if (has2d) shear_consts_2h(T(0.5) * q2z * xang, r.t2, r.s2, r.n2);
+  }
+  return r;
 }
 
 // --------------------------------------------------------- block reductions
@@ -157,36 +241,61 @@ template <class T> struct ColAcc {
 // their values with shuffles: the up-thread then owns positions m < E/2 of
 // both components, the down-thread positions m >= E/2; they swap back after.
 
-template <class T, int LOGN, int LOGE, int F>
-__global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass(const RowArgs a) {
+// R_end and/or R_start at this thread's H points (both components).
+template <class T, int LOGN, int LOGE, int F, bool FAST>
+__device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&pd)[(1 << LOGE) / 2], int t, int comp,
+                                         int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T g11, T g22,
+                                         T g12, T htau, T xang, int pieces, double (&nsum)[2]) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
   constexpr bool IMAG = (F & F_IMAG) != 0;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
-  const int half = min(16, (int)blockDim.x / 2);
-  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
-  const int tx = threadIdx.x;
-  const int comp = (tx / half) & 1;
-  const int tp = (tx % half) + half * (tx / (2 * half));
-  const int lrow = tp / TT, t = tp - lrow * TT;
-  const int inst = blockIdx.y;
-  const int y = blockIdx.x * a.rows + lrow;
-  cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N;
-  const void *tw = a.tw;
-  constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
-  const RowAcc<T> acc{sm + lrow * row_stride(N, sizeof(cx<T>)) + comp * PADN, 0};
-
-  cx<T> v[1][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[0][m] = p[t + m * TT];
-  if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
+  for (int j = 0; j < H; ++j) {
+    const int x = t + (j + comp * H) * TT;
+    cx<T> &u = pu[j];
+    cx<T> &d = pd[j];
+    const q4<T> px = tab[x];
+    T vu = px.x + ty.x, vd = px.y + ty.y;
+    T q2z = T(0);
+    if (p2) {
+      const q4<T> q = p2[(long)y * N + x];
+      vu += q.x;
+      vd += q.y;
+      q2z = q.z;
+    }
+    const XPoint<T> xc = xpoint<IMAG, T>(px, ty, p2 != nullptr, q2z, xang);
+    if constexpr (F & F_REND) {
+      applyX<IMAG>(u, d, xc, pieces);
+      opD<IMAG, FAST>(u, d, vu, vd, g11, g22, g12, htau);
+      applyX<IMAG>(u, d, xc, pieces);
+    }
+    if constexpr (F & F_PART) {
+      nsum[0] += double(cabs2(u));
+      nsum[1] += double(cabs2(d));
+    }
+    if constexpr (F & F_RSTART) {
+      applyX<IMAG>(u, d, xc, pieces);
+      opD<IMAG, FAST>(u, d, vu, vd, g11, g22, g12, htau);
+      applyX<IMAG>(u, d, xc, pieces);
+    }
+  }
+}
+
+// Row-pass compute on registers already loaded: v holds this thread's
+// component at positions t + m*TT of row y.  tab points at the instance's
+// x step table (global or shared memory).  Returns the FP64 atom-number
+// partials of the R_end result when F has F_PART.
+template <class T, int LOGN, int LOGE, int F>
+__device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int comp, unsigned mask, int half,
+                                            int inst, int y, const RowAcc<T> &acc, const q4<T> *tab,
+                                            const RowArgs &a, double (&nsum)[2]) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
+  constexpr bool IMAG = (F & F_IMAG) != 0;
+  if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 1>(v, t, a.tw, acc);
   if constexpr (F & F_SCALE) {
     const T sc = T(a.scale[2 * inst + comp]);
 #pragma unroll
     for (int m = 0; m < E; ++m) v[0][m] = cscale(v[0][m], sc);
   }
-
-  double nsum[2] = {0.0, 0.0};
   if constexpr (F & (F_REND | F_RSTART)) {
     // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
     cx<T> pu[H], pd[H];
@@ -198,42 +307,28 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass(const RowArgs a) 
       pd[j] = comp ? v[0][H + j] : rcv;
     }
     const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
-    const q4<T> *tx4 = reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
     const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
-    const T g11 = T(a.gpar[4 * inst]), g22 = T(a.gpar[4 * inst + 1]), g12 = T(a.gpar[4 * inst + 2]);
-    const T htau = T(IMAG ? -a.tau : -0.5 * a.tau), xang = T(a.xang);
+    const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
+    const T g11 = gp[0], g22 = gp[1], g12 = gp[2];
+    T htau, xang;
+    if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
+    const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
+    // One code path per warp: the small-phase series when, for every point of
+    // the warp, |htau e| stays below the series' range.  e <= Vb + G rho_tot with
+    // Vb = max |V +- delta/2| of the instance and G = max(|g11|, |g22|) + |g12|;
+    // rho_tot = |u|^2 + |d|^2 at a point is left unchanged by real-time R
+    // (5 % margin for the imaginary-time X).
+    T rmax = T(0);
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const int x = t + (j + comp * H) * TT;
-      cx<T> &u = pu[j];
-      cx<T> &d = pd[j];
-      const q4<T> px = tx4[x];
-      T vu = px.x + ty.x, vd = px.y + ty.y;
-      T c = px.z, s = px.w;
-      rot_compose<IMAG>(c, s, ty.z, ty.w);
-      if (p2) {
-        const q4<T> q = p2[(long)y * N + x];
-        vu += q.x;
-        vd += q.y;
-        T c2, s2;
-        rot_of<IMAG>(q.z * xang, c2, s2);
-        rot_compose<IMAG>(c, s, c2, s2);
-      }
-      if constexpr (F & F_REND) {
-        opX<IMAG>(u, d, c, s);
-        opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
-        opX<IMAG>(u, d, c, s);
-      }
-      if constexpr (F & F_PART) {
-        nsum[0] += double(cabs2(u));
-        nsum[1] += double(cabs2(d));
-      }
-      if constexpr (F & F_RSTART) {
-        opX<IMAG>(u, d, c, s);
-        opD<IMAG>(u, d, vu, vd, g11, g22, g12, htau);
-        opX<IMAG>(u, d, c, s);
-      }
-    }
+    for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
+                                                      d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
+    const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
+    const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
+    const bool fast = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
+    if (fast)
+      r_points<T, LOGN, LOGE, F, true>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, nsum);
+    else
+      r_points<T, LOGN, LOGE, F, false>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, nsum);
     // scatter back to one component per thread
 #pragma unroll
     for (int j = 0; j < H; ++j) {
@@ -243,75 +338,101 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass(const RowArgs a) 
       v[0][H + j] = comp ? pd[j] : rcv;
     }
   }
+  if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 1>(v, t, a.tw, acc);
+}
 
-  if constexpr (F & F_PART) {
-    // FP64 atom-number partials; the last block of this instance reduces them
-    // in a fixed order and writes the renormalisation scale (Sec. 3.2).
-    __shared__ int s_last;
-    block_sum<2>(nsum);
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
-      a.partials[((long)inst * G + blockIdx.x) * 2] = nsum[0];
-      a.partials[((long)inst * G + blockIdx.x) * 2 + 1] = nsum[1];
-      __threadfence();
-      const unsigned prev = atomicAdd(&a.counters[inst], 1u);
-      s_last = (prev == (unsigned)G - 1u);
+// FP64 atom-number partials of one row group; the last group of the
+// instance to finish reduces them in a fixed order and writes the
+// renormalisation scale (Sec. 3.2).  Called by every thread of the block.
+__device__ __forceinline__ void row_partials(const RowArgs &a, int inst, int group, int ngroups, double (&nsum)[2]) {
+  __shared__ int s_last;
+  block_sum<2>(nsum);
+  if (threadIdx.x == 0) {
+    a.partials[((long)inst * ngroups + group) * 2] = nsum[0];
+    a.partials[((long)inst * ngroups + group) * 2 + 1] = nsum[1];
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.counters[inst], 1u);
+    s_last = (prev == (unsigned)ngroups - 1u);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double tot[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < ngroups; b += blockDim.x) {
+      tot[0] += __ldcg(&a.partials[((long)inst * ngroups + b) * 2]);
+      tot[1] += __ldcg(&a.partials[((long)inst * ngroups + b) * 2 + 1]);
     }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double tot[2] = {0.0, 0.0};
-      for (int b = threadIdx.x; b < G; b += blockDim.x) {
-        tot[0] += __ldcg(&a.partials[((long)inst * G + b) * 2]);
-        tot[1] += __ldcg(&a.partials[((long)inst * G + b) * 2 + 1]);
+    block_sum<2>(tot);
+    if (threadIdx.x == 0) {
+      const double nu = tot[0] * a.wgt, nd = tot[1] * a.wgt;
+      double s0, s1;
+      if (a.norm_mode == 1) {
+        s0 = sqrt(a.tgt0 / nu);
+        s1 = sqrt(a.tgt1 / nd);
+      } else {
+        s0 = s1 = sqrt((a.tgt0 + a.tgt1) / (nu + nd));
       }
-      block_sum<2>(tot);
-      if (threadIdx.x == 0) {
-        const double nu = tot[0] * a.wgt, nd = tot[1] * a.wgt;
-        double s0, s1;
-        if (a.norm_mode == 1) {
-          s0 = sqrt(a.tgt0 / nu);
-          s1 = sqrt(a.tgt1 / nd);
-        } else {
-          s0 = s1 = sqrt((a.tgt0 + a.tgt1) / (nu + nd));
-        }
-        if (!isfinite(s0) || !isfinite(s1)) atomicOr(a.flags, 1);
-        a.scale[2 * inst] = s0;
-        a.scale[2 * inst + 1] = s1;
-        a.counters[inst] = 0u;
-      }
+      if (!isfinite(s0) || !isfinite(s1)) atomicOr(a.flags, 1);
+      a.scale[2 * inst] = s0;
+      a.scale[2 * inst + 1] = s1;
+      a.counters[inst] = 0u;
     }
   }
+  __syncthreads();
+}
 
-  if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);
+// Thread placement of the row pass (see above).
+struct RowPlace {
+  int half, comp, lrow, t;
+  unsigned mask;
+};
+template <int TT> __device__ __forceinline__ RowPlace row_place() {
+  RowPlace r;
+  r.half = min(16, (int)blockDim.x / 2);
+  r.mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  const int tx = threadIdx.x;
+  r.comp = (tx / r.half) & 1;
+  const int tp = (tx % r.half) + r.half * (tx / (2 * r.half));
+  r.lrow = tp / TT;
+  r.t = tp - r.lrow * TT;
+  return r;
+}
+
+template <class T, int LOGN, int LOGE, int F>
+__global__ void __launch_bounds__(LOGN <= 11 ? kRowMaxThreads : 2 * kRowMaxThreads, sizeof(T) == 4 && LOGN <= 11 ? 3 : 1)
+row_pass(const RowArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+  const RowPlace pl = row_place<TT>();
+  const int inst = blockIdx.y;
+  const int y = blockIdx.x * a.rows + pl.lrow;
+  cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + pl.comp) * a.ny + y) * N;
+  constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
+  const RowAcc<T> acc{sm + pl.lrow * row_stride(N, sizeof(cx<T>)) + pl.comp * PADN, 0};
+
+  cx<T> v[1][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) p[t + m * TT] = v[0][m];
+  for (int m = 0; m < E; ++m) v[0][m] = p[pl.t + m * TT];
+  double nsum[2] = {0.0, 0.0};
+  row_compute<T, LOGN, LOGE, F>(v, pl.t, pl.comp, pl.mask, pl.half, inst, y, acc,
+                                reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N, a, nsum);
+  if constexpr (F & F_PART) row_partials(a, inst, blockIdx.x, gridDim.x, nsum);
+#pragma unroll
+  for (int m = 0; m < E; ++m) p[pl.t + m * TT] = v[0][m];
 }
 
 // ---------------------------------------------------------- column pass
 
+// Column-pass compute on registers already loaded: forward y-FFT, K(dt) with
+// am = a_j(kx) - 1 and bm = b(ky) - 1 (global or shared), inverse y-FFT.
+// K' - 1 = (a-1)(b-1) + (a-1) + (b-1) is applied as z + (K' - 1) z and the
+// exact power of two 1/(nx ny) last.
 template <class T, int LOGN, int LOGE, bool IMAG>
-__global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
+__device__ __forceinline__ void col_compute(cx<T> (&v)[1][1 << LOGE], int t, const ColAcc<T> &acc, const void *tw,
+                                            cx<T> am, const cx<T> *bm, T inv) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int C = a.C;
-  const int c = threadIdx.x % C, t = threadIdx.x / C;
-  const int comp = blockIdx.y, inst = blockIdx.z;
-  const int kx = blockIdx.x * C + c;
-  cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + ((long)inst * 2 + comp) * (long)N * a.nx + kx;
-  const void *tw = a.tw;
-  const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
-  const int rs = TT * a.nx;  // element offset between a thread's rows (fits in 32 bits)
-
-  cx<T> v[1][E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) v[0][m] = col[t * a.nx + m * rs];
   block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);
-  // K(dt) = a_j(kx) b(ky) / (nx ny) as z + (K' - 1) z, K' - 1 = (a-1)(b-1) + (a-1) + (b-1);
-  // the exact power of two 1/(nx ny) is applied last.
-  const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
-  const cx<T> *bm = reinterpret_cast<const cx<T> *>(a.kyt);
-  const T inv = T(1) / T((long)a.nx * N);
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const cx<T> b = bm[t + m * TT];
@@ -327,6 +448,27 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
     v[0][m] = {z.re * inv, z.im * inv};
   }
   block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
+}
+
+template <class T, int LOGN, int LOGE, bool IMAG>
+__global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int C = a.C;
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  const int comp = blockIdx.y, inst = blockIdx.z;
+  const int kx = blockIdx.x * C + c;
+  cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + ((long)inst * 2 + comp) * (long)N * a.nx + kx;
+  const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
+  const int rs = TT * a.nx;  // element offset between a thread's rows (fits in 32 bits)
+
+  cx<T> v[1][E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[0][m] = col[t * a.nx + m * rs];
+  const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
+  T inv;
+  if constexpr (sizeof(T) == 4) inv = a.inv_f; else inv = a.inv_d;
+  col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, reinterpret_cast<const cx<T> *>(a.kyt), inv);
 #pragma unroll
   for (int m = 0; m < E; ++m) col[t * a.nx + m * rs] = v[0][m];
 }
@@ -340,7 +482,7 @@ __device__ __forceinline__ int kbin(int i, int n) { return i < n / 2 ? i : i - n
 template <class T, int LOGN, int LOGE>
 __global__ void __launch_bounds__(2 * kRowMaxThreads) energy_row(const EnergyArgs a) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
   const int lrow = threadIdx.x / TT, t = threadIdx.x - lrow * TT;
   const int inst = blockIdx.y;
@@ -398,7 +540,7 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) energy_row(const EnergyArg
 template <class T, int LOGN, int LOGE>
 __global__ void __launch_bounds__(512) energy_col(const EnergyArgs a) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int C = a.C;
   const int c = threadIdx.x % C, t = threadIdx.x / C;
   const int comp = blockIdx.y, inst = blockIdx.z;
@@ -476,21 +618,23 @@ __global__ void __launch_bounds__(256) ref_R_kernel(const RowArgs a) {
   cx<T> *d = u + plane;
   const q4<T> px = reinterpret_cast<const q4<T> *>(a.tabx)[(long)inst * a.nx + x];
   const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
-  T vu = px.x + ty.x, vd = px.y + ty.y, c = px.z, s = px.w;
-  rot_compose<IMAG>(c, s, ty.z, ty.w);
-  if (a.pot2d) {
+  T vu = px.x + ty.x, vd = px.y + ty.y, q2z = T(0);
+  const bool has2d = a.pot2d != nullptr;
+  if (has2d) {
     const q4<T> q = reinterpret_cast<const q4<T> *>(a.pot2d)[i];
     vu += q.x;
     vd += q.y;
-    T c2, s2;
-    rot_of<IMAG>(q.z * T(a.xang), c2, s2);
-    rot_compose<IMAG>(c, s, c2, s2);
+    q2z = q.z;
   }
+  T htau, xang;
+  if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
+  const XPoint<T> xc = xpoint<IMAG, T>(px, ty, has2d, q2z, xang);
+  const int pieces = (a.omega_pieces & 3) | (has2d ? 4 : 0);
+  const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
   cx<T> U = *u, D = *d;
-  opX<IMAG>(U, D, c, s);
-  opD<IMAG>(U, D, vu, vd, T(a.gpar[4 * inst]), T(a.gpar[4 * inst + 1]), T(a.gpar[4 * inst + 2]),
-            T(IMAG ? -a.tau : -0.5 * a.tau));
-  opX<IMAG>(U, D, c, s);
+  applyX<IMAG>(U, D, xc, pieces);
+  opD<IMAG>(U, D, vu, vd, gp[0], gp[1], gp[2], htau);
+  applyX<IMAG>(U, D, xc, pieces);
   *u = U;
   *d = D;
 }

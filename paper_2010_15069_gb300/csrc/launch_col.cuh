@@ -3,15 +3,14 @@
 #pragma once
 #include <algorithm>
 
-#include "kernels.cuh"
+#include "kernels_persist.cuh"
 
 namespace spgpe {
 
 // Elements per thread of the column pass (one component per thread): 16
-// complex64 / 8 complex128, doubled from 2048 up so that a block still spans
-// several adjacent columns.
+// complex64 / 8 complex128 (16 from 2048 up, so that a column fits 512 threads).
 template <class T> constexpr int col_loge(int logn) {
-  return sizeof(T) == 4 ? (logn >= 11 ? 5 : std::min(logn, 4)) : (logn >= 11 ? 4 : std::min(logn, 3));
+  return sizeof(T) == 4 ? std::min(logn, 4) : (logn >= 11 ? 4 : std::min(logn, 3));
 }
 
 template <class T> LaunchShape col_shape(int nx, int ny) {
@@ -30,7 +29,7 @@ template <class T> LaunchShape col_shape(int nx, int ny) {
   return s;
 }
 
-template <class K> cudaError_t grant_smem(K kern, size_t smem, int &granted) {
+template <class K> cudaError_t grant_smem_c(K kern, size_t smem, int &granted) {
   if ((int)smem > granted) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -44,7 +43,7 @@ template <class T, int LOGN, bool IMAG> cudaError_t col_launch_n(ColArgs a, cuda
   auto kern = col_pass<T, LOGN, LOGE, IMAG>;
   const LaunchShape sh = col_shape<T>(a.nx, a.ny);
   static int granted = 0;
-  cudaError_t e = grant_smem(kern, sh.smem, granted);
+  cudaError_t e = grant_smem_c(kern, sh.smem, granted);
   if (e != cudaSuccess) return e;
   a.C = sh.rows_or_cols;
   kern<<<dim3(sh.blocks_x, 2, a.ninst), sh.threads, sh.smem, st>>>(a);
@@ -63,7 +62,7 @@ template <class T, int LOGN> cudaError_t energy_launch_n(EnergyArgs a, cudaStrea
     const int rows = std::max(1, std::min(kRowMaxThreads / TT, a.ny));
     const size_t smem = (size_t)rows * row_stride(a.nx, sizeof(cx<T>)) * sizeof(cx<T>);
     static int granted = 0;
-    cudaError_t e = grant_smem(kern, smem, granted);
+    cudaError_t e = grant_smem_c(kern, smem, granted);
     if (e != cudaSuccess) return e;
     a.rows = rows;
     *rb = a.ny / rows;
@@ -79,7 +78,7 @@ template <class T, int LOGN> cudaError_t energy_col_launch_n(EnergyArgs a, cudaS
   auto kern = energy_col<T, LOGN, LOGE>;
   const LaunchShape sh = col_shape<T>(a.nx, a.ny);
   static int granted = 0;
-  cudaError_t e = grant_smem(kern, sh.smem, granted);
+  cudaError_t e = grant_smem_c(kern, sh.smem, granted);
   if (e != cudaSuccess) return e;
   a.C = sh.rows_or_cols;
   *cb = sh.blocks_x;
@@ -149,6 +148,64 @@ template <class T> cudaError_t launch_residual(const void *psi, const void *prev
   return cudaGetLastError();
 }
 
+// ---- persistent column pass
+
+// Columns per tile of the persistent pass: a 128-byte row segment where two
+// tile buffers fit in about 110 KB and the block stays within 512 threads;
+// at least 16 bytes (one TMA row of 8-byte elements).
+template <class T> int colp_cols(int nx, int ny) {
+  int logn = 0;
+  while ((1 << logn) < ny) ++logn;
+  const int E = 1 << col_loge<T>(logn);
+  const int TT = ny / E;
+  const int es = sizeof(cx<T>);
+  int C = std::min(128 / es, nx);
+  while (C > 1 && (C * TT > kColMaxThreads || kPipe * colp_buf_bytes(ny, C, es) > 112 * 1024)) C /= 2;
+  if (C * es < 16) C = 16 / es;
+  return C;
+}
+
+template <class T, int LOGN, bool IMAG>
+cudaError_t colp_launch_n(ColArgs a, const CUtensorMap &map, cudaStream_t st, int sms) {
+  constexpr int LOGE = col_loge<T>(LOGN);
+  constexpr int N = 1 << LOGN, TT = N >> LOGE;
+  auto kern = col_pass_p<T, LOGN, LOGE, IMAG>;
+  const int C = colp_cols<T>(a.nx, a.ny);
+  const int threads = C * TT;
+  const int es = sizeof(cx<T>);
+  const size_t smem = kPipe * colp_buf_bytes(N, C, es) + (size_t)N * es + kPipe * sizeof(uint64_t);
+  if (smem > kMaxSmemPerBlock) return cudaErrorNotSupported;  // caller falls back to the plain pass
+  static int granted = 0;
+  cudaError_t e = grant_smem_c(kern, smem, granted);
+  if (e != cudaSuccess) return e;
+  static int occ_threads = -1, occ_blocks = 0;
+  static size_t occ_smem = 0;
+  if (occ_threads != threads || occ_smem != smem) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    occ_threads = threads;
+    occ_smem = smem;
+  }
+  const int ntiles = (a.nx / C) * 2 * a.ninst;
+  const int grid = std::max(1, std::min(ntiles, std::max(1, occ_blocks) * sms));
+  a.C = C;
+  kern<<<grid, threads, smem, st>>>(map, a, ntiles);
+  return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_col_p(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t st,
+                                            int sms) {
+#define SPGPE_COLP_REAL(L) colp_launch_n<T, L, false>(a, map, st, sms)
+#define SPGPE_COLP_IMAG(L) colp_launch_n<T, L, true>(a, map, st, sms)
+  if (imag) {
+    SPGPE_SWITCH_LOGN(a.ny, SPGPE_COLP_IMAG)
+  } else {
+    SPGPE_SWITCH_LOGN(a.ny, SPGPE_COLP_REAL)
+  }
+#undef SPGPE_COLP_REAL
+#undef SPGPE_COLP_IMAG
+}
+
 template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t st) {
   const long plane = (long)a.nx * a.ny;
   ref_K_kernel<T><<<dim3((unsigned)((plane + 255) / 256), 2 * a.ninst), 256, 0, st>>>(a);
@@ -162,6 +219,8 @@ template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t st) {
   template cudaError_t launch_norm<T>(const void *, long, int, double *, int, cudaStream_t);  \
   template cudaError_t launch_residual<T>(const void *, const void *, long, int, double *, int, \
                                           cudaStream_t);                                      \
-  template cudaError_t launch_ref_K<T>(const ColArgs &, cudaStream_t);
+  template cudaError_t launch_ref_K<T>(const ColArgs &, cudaStream_t);                      \
+  template int colp_cols<T>(int, int);                                                        \
+  template cudaError_t launch_col_p<T>(bool, ColArgs, const CUtensorMap &, cudaStream_t, int);
 
 }  // namespace spgpe

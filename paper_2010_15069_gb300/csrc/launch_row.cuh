@@ -3,7 +3,7 @@
 #pragma once
 #include <algorithm>
 
-#include "kernels.cuh"
+#include "kernels_persist.cuh"
 
 namespace spgpe {
 
@@ -27,6 +27,15 @@ template <class T> LaunchShape row_shape(int nx, int ny) {
   s.rows_or_cols = rows;
   s.smem = (size_t)rows * row_stride(nx, sizeof(cx<T>)) * sizeof(cx<T>);
   return s;
+}
+
+template <class K> cudaError_t grant_smem(K kern, size_t smem, int &granted) {
+  if ((int)smem > granted) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    granted = (int)smem;
+  }
+  return cudaSuccess;
 }
 
 template <class T, int LOGN, int F> cudaError_t row_launch_n(RowArgs a, cudaStream_t st) {
@@ -73,6 +82,76 @@ template <class T> cudaError_t launch_row(int flags, RowArgs a, cudaStream_t st)
   }
 }
 
+// ---- persistent row pass
+
+// Rows per tile of the persistent pass: about 256 threads per block.
+template <class T> int rowp_rows(int nx, int ny) {
+  int logn = 0;
+  while ((1 << logn) < nx) ++logn;
+  const int TT = nx >> row_loge<T>(logn);
+  return std::max(1, std::min(kRowMaxThreads / (2 * TT), ny));
+}
+
+template <class T, int LOGN, int F> cudaError_t rowp_launch_n(RowArgs a, cudaStream_t st, int sms) {
+  constexpr int LOGE = row_loge<T>(LOGN);
+  constexpr int N = 1 << LOGN, TT = N >> LOGE;
+  constexpr bool NEEDTAB = (F & (F_REND | F_RSTART)) != 0;
+  auto kern = row_pass_p<T, LOGN, LOGE, F>;
+  const int rows = rowp_rows<T>(a.nx, a.ny);
+  const int threads = 2 * rows * TT;
+  const int es = sizeof(cx<T>);
+  // copy the x step table with each tile while two tile buffers stay under ~110 KB
+  bool tab = NEEDTAB && kPipe * rowp_buf_bytes(N, rows, es, true) <= 112 * 1024;
+  const size_t smem = kPipe * rowp_buf_bytes(N, rows, es, tab) + kPipe * sizeof(uint64_t);
+  if (smem > kMaxSmemPerBlock) return cudaErrorNotSupported;  // caller falls back to the plain pass
+  static int granted = 0;
+  cudaError_t e = grant_smem(kern, smem, granted);
+  if (e != cudaSuccess) return e;
+  static int occ_threads = -1, occ_blocks = 0;
+  static size_t occ_smem = 0;
+  if (occ_threads != threads || occ_smem != smem) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    occ_threads = threads;
+    occ_smem = smem;
+  }
+  const int ntiles = a.ninst * (a.ny / rows);
+  const int grid = std::max(1, std::min(ntiles, std::max(1, occ_blocks) * sms));
+  a.rows = rows;
+  a.tab_in_smem = tab ? 1 : 0;
+  kern<<<grid, threads, smem, st>>>(a, ntiles);
+  return cudaGetLastError();
+}
+
+template <class T, int LOGN> cudaError_t rowp_launch_f(int flags, const RowArgs &a, cudaStream_t st, int sms) {
+  switch (flags) {
+    case kRealFirst: return rowp_launch_n<T, LOGN, kRealFirst>(a, st, sms);
+    case kRealMid: return rowp_launch_n<T, LOGN, kRealMid>(a, st, sms);
+    case kRealLast: return rowp_launch_n<T, LOGN, kRealLast>(a, st, sms);
+    case kImagFirst: return rowp_launch_n<T, LOGN, kImagFirst>(a, st, sms);
+    case kImagB: return rowp_launch_n<T, LOGN, kImagB>(a, st, sms);
+    case kImagA: return rowp_launch_n<T, LOGN, kImagA>(a, st, sms);
+    case kImagScale: return rowp_launch_n<T, LOGN, kImagScale>(a, st, sms);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T> cudaError_t launch_row_p(int flags, RowArgs a, cudaStream_t st, int sms) {
+  switch (a.nx) {
+    case 8: return rowp_launch_f<T, 3>(flags, a, st, sms);
+    case 16: return rowp_launch_f<T, 4>(flags, a, st, sms);
+    case 32: return rowp_launch_f<T, 5>(flags, a, st, sms);
+    case 64: return rowp_launch_f<T, 6>(flags, a, st, sms);
+    case 128: return rowp_launch_f<T, 7>(flags, a, st, sms);
+    case 256: return rowp_launch_f<T, 8>(flags, a, st, sms);
+    case 512: return rowp_launch_f<T, 9>(flags, a, st, sms);
+    case 1024: return rowp_launch_f<T, 10>(flags, a, st, sms);
+    case 2048: return rowp_launch_f<T, 11>(flags, a, st, sms);
+    case 4096: return rowp_launch_f<T, 12>(flags, a, st, sms);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStream_t st) {
   const long plane = (long)a.nx * a.ny;
   const dim3 grid((unsigned)((plane + 255) / 256), a.ninst);
@@ -84,6 +163,7 @@ template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStr
 #define SPGPE_INSTANTIATE_ROW(T)                                                    \
   template LaunchShape row_shape<T>(int, int);                                      \
   template cudaError_t launch_row<T>(int, RowArgs, cudaStream_t);                   \
-  template cudaError_t launch_ref_R<T>(bool, const RowArgs &, cudaStream_t);
+  template cudaError_t launch_ref_R<T>(bool, const RowArgs &, cudaStream_t);         \
+  template cudaError_t launch_row_p<T>(int, RowArgs, cudaStream_t, int);
 
 }  // namespace spgpe

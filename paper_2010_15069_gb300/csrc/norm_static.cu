@@ -11,7 +11,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "../../include/spgpe.h"
+#include "spgpe.h"
 #include "internal.h"
 #include "kernels.cuh"
 
