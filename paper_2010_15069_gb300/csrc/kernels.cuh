@@ -230,6 +230,17 @@ template <class T> struct ColAcc {
   __device__ __forceinline__ cx<T> ld(int, int p) const { return base[idx(p)]; }
 };
 
+// Same layout with the tile width known at compile time: for C a multiple of
+// the 128-byte line (in elements) the padding term is linear in p and every
+// exchange address folds into a per-thread base plus an immediate offset.
+template <class T, int C> struct ColAccC {
+  static constexpr int SH = pad_shift(sizeof(cx<T>));
+  cx<T> *base;  // already offset by the thread's column
+  __device__ __forceinline__ static int idx(int p) { return p * C + ((p * C) >> SH); }
+  __device__ __forceinline__ void st(int, int p, cx<T> v) const { base[idx(p)] = v; }
+  __device__ __forceinline__ cx<T> ld(int, int p) const { return base[idx(p)]; }
+};
+
 // ------------------------------------------------------------- row pass
 //
 // Each row is held by 2*TT threads: TT threads per component, E values each.
@@ -428,8 +439,8 @@ row_pass(const RowArgs a) {
 // am = a_j(kx) - 1 and bm = b(ky) - 1 (global or shared), inverse y-FFT.
 // K' - 1 = (a-1)(b-1) + (a-1) + (b-1) is applied as z + (K' - 1) z and the
 // exact power of two 1/(nx ny) last.
-template <class T, int LOGN, int LOGE, bool IMAG>
-__device__ __forceinline__ void col_compute(cx<T> (&v)[1][1 << LOGE], int t, const ColAcc<T> &acc, const void *tw,
+template <class T, int LOGN, int LOGE, bool IMAG, class Acc>
+__device__ __forceinline__ void col_compute(cx<T> (&v)[1][1 << LOGE], int t, const Acc &acc, const void *tw,
                                             cx<T> am, const cx<T> *bm, T inv) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
   block_fft<LOGN, LOGE, -1, 1>(v, t, tw, acc);

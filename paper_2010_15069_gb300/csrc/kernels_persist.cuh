@@ -19,6 +19,11 @@ namespace spgpe {
 
 constexpr int kPipe = 2;  // tile buffers per block
 
+// Shared-memory plan of the persistent column pass.
+__host__ __device__ constexpr size_t colp_buf_bytes(int n, int c, int es) {
+  return ((size_t)col_smem_elems(n, c, es) * es + 127) / 128 * 128;
+}
+
 // A wait for tile i ran out: record the error, then give the other copy this
 // block still has in flight (tile + gridDim.x, if it was issued) its own
 // bounded wait, so the block does not exit with a transfer landing in its
@@ -108,22 +113,27 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass_p(const RowArgs a
   }
 }
 
-// Shared-memory plan of the persistent column pass.
-__host__ __device__ constexpr size_t colp_buf_bytes(int n, int c, int es) {
-  return ((size_t)col_smem_elems(n, c, es) * es + 127) / 128 * 128;
+
+// Columns per tile of the persistent column pass: a 128-byte row segment
+// where two tile buffers fit in about 110 KB and the block stays within 512
+// threads; at least 16 bytes (one TMA row of 8-byte elements).
+template <class T> __host__ __device__ constexpr int colp_cols_c(int logn, int loge) {
+  const int n = 1 << logn, tt = n >> loge, es = (int)sizeof(cx<T>);
+  int c = 128 / es;
+  while (c > 1 && (c * tt > kColMaxThreads || kPipe * colp_buf_bytes(n, c, es) > 112 * 1024)) c /= 2;
+  if (c * es < 16) c = 16 / es;
+  return c;
 }
 
-template <class T, int LOGN, int LOGE, bool IMAG>
+template <class T, int LOGN, int LOGE, bool IMAG, int C>
 __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
-    col_pass_p(const __grid_constant__ CUtensorMap map, const ColArgs a,
-                                                   int ntiles) {
+    col_pass_p(const __grid_constant__ CUtensorMap map, const ColArgs a, int ntiles) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
   constexpr int ES = sizeof(cx<T>);
   constexpr int XMUL = ES / 8;             // tensor-map elements per complex value
   constexpr int BOXH = N < 256 ? N : 256;  // rows per TMA box
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int C = a.C;
-  const size_t bufb = colp_buf_bytes(N, C, ES);
+  constexpr size_t bufb = colp_buf_bytes(N, C, ES);
   cx<T> *btab = reinterpret_cast<cx<T> *>(smem_raw + kPipe * bufb);
   uint64_t *bar = reinterpret_cast<uint64_t *>(btab + N);
   const int c = threadIdx.x % C, t = threadIdx.x / C;
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     for (int m = 0; m < E; ++m) v[0][m] = b[(t + m * TT) * C + c];
     const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[(long)pc * a.nx + kx];
     __syncthreads();  // the dense tile is read; its space now serves the exchanges
-    const ColAcc<T> acc{b, C, c};
+    const ColAccC<T, C> acc{b + c};
     col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, btab, inv);
     cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + (long)pc * N * a.nx + kx;
     const int rs = TT * a.nx;

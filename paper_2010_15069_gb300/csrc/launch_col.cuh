@@ -150,27 +150,19 @@ template <class T> cudaError_t launch_residual(const void *psi, const void *prev
 
 // ---- persistent column pass
 
-// Columns per tile of the persistent pass: a 128-byte row segment where two
-// tile buffers fit in about 110 KB and the block stays within 512 threads;
-// at least 16 bytes (one TMA row of 8-byte elements).
 template <class T> int colp_cols(int nx, int ny) {
   int logn = 0;
   while ((1 << logn) < ny) ++logn;
-  const int E = 1 << col_loge<T>(logn);
-  const int TT = ny / E;
-  const int es = sizeof(cx<T>);
-  int C = std::min(128 / es, nx);
-  while (C > 1 && (C * TT > kColMaxThreads || kPipe * colp_buf_bytes(ny, C, es) > 112 * 1024)) C /= 2;
-  if (C * es < 16) C = 16 / es;
-  return C;
+  return colp_cols_c<T>(logn, col_loge<T>(logn));
 }
 
 template <class T, int LOGN, bool IMAG>
 cudaError_t colp_launch_n(ColArgs a, const CUtensorMap &map, cudaStream_t st, int sms) {
   constexpr int LOGE = col_loge<T>(LOGN);
   constexpr int N = 1 << LOGN, TT = N >> LOGE;
-  auto kern = col_pass_p<T, LOGN, LOGE, IMAG>;
-  const int C = colp_cols<T>(a.nx, a.ny);
+  constexpr int C = colp_cols_c<T>(LOGN, LOGE);
+  if (a.nx < C) return cudaErrorNotSupported;  // narrower than one tile: the plain pass
+  auto kern = col_pass_p<T, LOGN, LOGE, IMAG, C>;
   const int threads = C * TT;
   const int es = sizeof(cx<T>);
   const size_t smem = kPipe * colp_buf_bytes(N, C, es) + (size_t)N * es + kPipe * sizeof(uint64_t);
