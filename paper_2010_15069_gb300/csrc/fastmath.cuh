@@ -71,7 +71,25 @@ __device__ __forceinline__ void expi2_m1(float h, float &wre, float &wim) {
 // common case of a small phase costs a handful of fma:
 // tan h = h + h^3/3 + 2h^5/15 + 17h^7/315 + 62h^9/2835 + ...,
 // sin 2h = 2h - 4h^3/3 + 4h^5/15 - 8h^7/315 + 4h^9/2835 - ...
+// The general tiers live out of line: kernels inline only the warp-uniform
+// small-phase series, and a single copy of this routine serves the rare
+// warps with larger phases (keeps the row pass within the instruction cache).
+struct ShearConsts {
+  float t, s;
+  int neg;
+};
+static __device__ __noinline__ ShearConsts shear_consts_2h_general(float h);
+
 __device__ __forceinline__ void shear_consts_2h(float h, float &t, float &s, bool &neg) {
+  const ShearConsts r = shear_consts_2h_general(h);
+  t = r.t;
+  s = r.s;
+  neg = r.neg != 0;
+}
+
+static __device__ __noinline__ ShearConsts shear_consts_2h_general(float h) {
+  float t, s;
+  bool neg;
   const float ah = fabsf(h);
   neg = false;
   if (ah < 0.03125f) {  // truncation below 2e-11 relative
@@ -104,6 +122,7 @@ __device__ __forceinline__ void shear_consts_2h(float h, float &t, float &s, boo
     s = 2.0f * sr * cr;
     neg = (n & 1) != 0;  // exp(2ih) = -exp(2ir)
   }
+  return ShearConsts{t, s, neg ? 1 : 0};
 }
 
 // The middle tier alone, for callers that know |h| < 1/8 for a whole warp.

@@ -200,12 +200,12 @@ __device__ __forceinline__ void fft_stages(cx<T> (&v)[NSEQ][1 << LOGE], int t,
     constexpr bool LAST = (STAGE == P::S - 1);
     fft_stage<N, E, R, NS, LAST, SIGN, NSEQ>(v, t, tw, acc);
     if constexpr (!LAST) {
-      __syncthreads();
+      acc.sync();
 #pragma unroll
       for (int q = 0; q < NSEQ; ++q)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[q][m] = acc.ld(q, t + m * TT);
-      __syncthreads();
+      acc.sync();
       fft_stages<LOGN, LOGE, SIGN, NSEQ, STAGE + 1>(v, t, tw, acc);
     }
   }
@@ -213,7 +213,8 @@ __device__ __forceinline__ void fft_stages(cx<T> (&v)[NSEQ][1 << LOGE], int t,
 
 // Length-2^LOGN transform of NSEQ sequences held as described above.
 // SIGN = -1 forward (unnormalised), +1 inverse (unnormalised).  Must be called
-// by every thread of the block (it synchronises the block between stages).
+// by every thread that acc.sync() synchronises (the block, or the warp when
+// all exchange partners of a sequence share a warp).
 template <int LOGN, int LOGE, int SIGN, int NSEQ, class T, class Acc>
 __device__ __forceinline__ void block_fft(cx<T> (&v)[NSEQ][1 << LOGE], int t, const void *tw_table,
                                           const Acc &acc) {

@@ -213,12 +213,19 @@ template <int K> __device__ __forceinline__ void block_sum(double (&v)[K]) {
 
 // ---------------------------------------------------- shared-memory layouts
 
-template <class T> struct RowAcc {
+// WARP_LOCAL: every thread that exchanges values with this one through
+// shared memory is in its warp (a row's threads never straddle warps), so the
+// stages synchronise with a warp barrier over `mask` instead of the block.
+template <class T, bool WARP_LOCAL = false> struct RowAcc {
   static constexpr int SH = pad_shift(sizeof(cx<T>));
   cx<T> *base;
   int stride;
+  unsigned mask;
   __device__ __forceinline__ void st(int q, int p, cx<T> v) const { base[q * stride + p + (p >> SH)] = v; }
   __device__ __forceinline__ cx<T> ld(int q, int p) const { return base[q * stride + p + (p >> SH)]; }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (WARP_LOCAL) __syncwarp(mask); else __syncthreads();
+  }
 };
 
 template <class T> struct ColAcc {
@@ -228,6 +235,7 @@ template <class T> struct ColAcc {
   __device__ __forceinline__ int idx(int p) const { const int e = p * C + c; return e + (e >> SH); }
   __device__ __forceinline__ void st(int, int p, cx<T> v) const { base[idx(p)] = v; }
   __device__ __forceinline__ cx<T> ld(int, int p) const { return base[idx(p)]; }
+  __device__ __forceinline__ static void sync() { __syncthreads(); }
 };
 
 // Same layout with the tile width known at compile time: for C a multiple of
@@ -239,6 +247,7 @@ template <class T, int C> struct ColAccC {
   __device__ __forceinline__ static int idx(int p) { return p * C + ((p * C) >> SH); }
   __device__ __forceinline__ void st(int, int p, cx<T> v) const { base[idx(p)] = v; }
   __device__ __forceinline__ cx<T> ld(int, int p) const { return base[idx(p)]; }
+  __device__ __forceinline__ static void sync() { __syncthreads(); }
 };
 
 // ------------------------------------------------------------- row pass
@@ -295,9 +304,9 @@ __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&p
 // component at positions t + m*TT of row y.  tab points at the instance's
 // x step table (global or shared memory).  Returns the FP64 atom-number
 // partials of the R_end result when F has F_PART.
-template <class T, int LOGN, int LOGE, int F>
+template <class T, int LOGN, int LOGE, int F, class Acc>
 __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int comp, unsigned mask, int half,
-                                            int inst, int y, const RowAcc<T> &acc, const q4<T> *tab,
+                                            int inst, int y, const Acc &acc, const q4<T> *tab,
                                             const RowArgs &a, double (&nsum)[2]) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
   constexpr bool IMAG = (F & F_IMAG) != 0;
@@ -392,7 +401,9 @@ __device__ __forceinline__ void row_partials(const RowArgs &a, int inst, int gro
   __syncthreads();
 }
 
-// Thread placement of the row pass (see above).
+// Thread placement of the row pass (see above).  With TT <= 16 threads per
+// component a row lies in one warp (or in the whole block, below 32 threads).
+__host__ __device__ constexpr bool row_warp_local(int tt) { return tt <= 16; }
 struct RowPlace {
   int half, comp, lrow, t;
   unsigned mask;
@@ -420,7 +431,8 @@ row_pass(const RowArgs a) {
   const int y = blockIdx.x * a.rows + pl.lrow;
   cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + pl.comp) * a.ny + y) * N;
   constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
-  const RowAcc<T> acc{sm + pl.lrow * row_stride(N, sizeof(cx<T>)) + pl.comp * PADN, 0};
+  const RowAcc<T, row_warp_local(TT)> acc{sm + pl.lrow * row_stride(N, sizeof(cx<T>)) + pl.comp * PADN, 0,
+                                          pl.mask};
 
   cx<T> v[1][E];
 #pragma unroll

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass_p(const RowArgs a
 #pragma unroll
     for (int m = 0; m < E; ++m) v[0][m] = b[(pl.comp * rows + pl.lrow) * N + pl.t + m * TT];
     __syncthreads();  // the dense tile is read; its space now serves the exchanges
-    const RowAcc<T> acc{b + pl.lrow * RS + pl.comp * PADN, 0};
+    const RowAcc<T, row_warp_local(TT)> acc{b + pl.lrow * RS + pl.comp * PADN, 0, pl.mask};
     const q4<T> *tab = tab_smem ? reinterpret_cast<const q4<T> *>(reinterpret_cast<unsigned char *>(b) +
                                                                   (size_t)rows * RS * ES)
                                 : reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
