@@ -125,6 +125,14 @@ static __device__ __noinline__ ShearConsts shear_consts_2h_general(float h) {
   return ShearConsts{t, s, neg ? 1 : 0};
 }
 
+// Cubic series, for callers that know |h| < 1/64 for a whole warp: the first
+// omitted terms (2h^5/15 and 4h^5/15) are below 8e-9 relative to t and s.
+__device__ __forceinline__ void shear_consts_2h_tiny(float h, float &t, float &s) {
+  const float h2 = h * h;
+  t = h * fmaf(h2, 0.33333333333f, 1.0f);
+  s = h * fmaf(h2, -1.3333333333f, 2.0f);
+}
+
 // The middle tier alone, for callers that know |h| < 1/8 for a whole warp.
 __device__ __forceinline__ void shear_consts_2h_small(float h, float &t, float &s) {
   const float h2 = h * h;

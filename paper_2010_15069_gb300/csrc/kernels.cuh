@@ -82,38 +82,47 @@ template <class T> __device__ __forceinline__ cx<T> add_mul1(cx<T> z, cx<T> w) {
 
 // D(tau): diagonal potential + mean-field phase (decay), densities on entry.
 // htau = -tau/2 in real time (the half phase), -tau in imaginary time.
-// FAST: the caller has checked, for the whole warp, that |htau e| < 1/8 (real
-// time) or < 1/2 (imaginary time), so the series need no range reduction.
-template <bool IMAG, bool FAST = false, class T>
+// TIER (the caller has checked it for every point of the warp): 0: |htau e|
+// < 1/64, 1: |htau e| < 1/8 (imaginary time: < 1/2), so the series need no
+// range reduction; 2: any phase.  FP64 always takes the library functions.
+template <bool IMAG, int TIER = 2, class T>
 __device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T htau) {
+  constexpr bool F32 = sizeof(T) == 4;
   const T ru = d_fma(u.re, u.re, u.im * u.im), rd = d_fma(d.re, d.re, d.im * d.im);
   const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
   const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
-  if constexpr (IMAG && FAST) {
-    const T fu = expm1_small(htau * eu), fd = expm1_small(htau * ed);
-    u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
-    d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
-  } else if constexpr (!IMAG && FAST) {
-    T tu, su, td, sd;
-    shear_consts_2h_small(htau * eu, tu, su);
-    shear_consts_2h_small(htau * ed, td, sd);
-    u = shear_rot(u, tu, su);
-    d = shear_rot(d, td, sd);
-  } else if constexpr (IMAG) {
-    const T fu = expm1_f(htau * eu), fd = expm1_f(htau * ed);
+  const T hu = htau * eu, hd = htau * ed;
+  if constexpr (IMAG) {
+    T fu, fd;
+    if constexpr (F32 && TIER < 2) {
+      fu = expm1_small(hu);
+      fd = expm1_small(hd);
+    } else {
+      fu = expm1_f(hu);
+      fd = expm1_f(hd);
+    }
     u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
     d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
   } else {
     // the phases exp(-i tau e) as three-shear rotations by 2 h, h = htau e
     // (determinant one: no systematic change of |psi| from rounded constants)
     T tu, su, td, sd;
-    bool nu, nd;
-    shear_consts_2h(htau * eu, tu, su, nu);
-    shear_consts_2h(htau * ed, td, sd, nd);
+    if constexpr (F32 && TIER == 0) {
+      shear_consts_2h_tiny(hu, tu, su);
+      shear_consts_2h_tiny(hd, td, sd);
+    } else if constexpr (F32 && TIER == 1) {
+      shear_consts_2h_small(hu, tu, su);
+      shear_consts_2h_small(hd, td, sd);
+    } else {
+      bool nu, nd;
+      shear_consts_2h(hu, tu, su, nu);
+      shear_consts_2h(hd, td, sd, nd);
+      // a rotation by 2r + pi: negate (commutes with the rotation by 2r)
+      if (nu) u = {-u.re, -u.im};
+      if (nd) d = {-d.re, -d.im};
+    }
     u = shear_rot(u, tu, su);
     d = shear_rot(d, td, sd);
-    if (nu) u = {-u.re, -u.im};
-    if (nd) d = {-d.re, -d.im};
   }
 }
 
@@ -157,6 +166,41 @@ __device__ __forceinline__ void applyX(cx<T> &u, cx<T> &d, const XPoint<T> &x, i
       }
     }
   }
+}
+
+// Real-time X applied twice in a row (the closing R(dt/2) of one step meets
+// the opening R(dt/2) of the next): the y piece as one rotation by the doubled
+// angle when (tm, sm) are its shear constants (ymerge), the other pieces
+// twice (their negations cancel).
+template <class T>
+__device__ __forceinline__ void applyX2(cx<T> &u, cx<T> &d, const XPoint<T> &x, int pieces, bool ymerge, T tm,
+                                        T sm) {
+  if (pieces & 1) {
+    if (ymerge) {
+      opXr(u, d, tm, sm);
+    } else {
+      opXr(u, d, x.m, x.s);
+      opXr(u, d, x.m, x.s);
+    }
+  }
+  if (pieces & 2) {
+    opXr(u, d, x.tx, x.sx);
+    opXr(u, d, x.tx, x.sx);
+  }
+  if (pieces & 4) {
+    opXr(u, d, x.t2, x.s2);
+    opXr(u, d, x.t2, x.s2);
+  }
+}
+
+// Shear constants of the doubled angle from (t, s) = (tan(a/2), sin a):
+// cos a = 1 - t s, so tan a = s / (1 - t s) and sin 2a = 2 s (1 - t s).
+// Valid (ymerge) while |a| < pi/4, i.e. cos a > 1/sqrt 2.
+template <class T> __device__ __forceinline__ bool x_double(T t, T s, T &tm, T &sm) {
+  const T c = d_fma(-t, s, T(1));
+  tm = s / c;
+  sm = T(2) * s * c;
+  return c > T(0.70710678118654752);
 }
 
 // X constants at point (x, y): px, ty are the x and y step-table entries,
@@ -262,12 +306,18 @@ template <class T, int C> struct ColAccC {
 // both components, the down-thread positions m >= E/2; they swap back after.
 
 // R_end and/or R_start at this thread's H points (both components).
-template <class T, int LOGN, int LOGE, int F, bool FAST>
+// MERGE (the fused real-time pass): X D X X D X with the middle X X as one
+// doubled X (exact: the two factors are the same rotation about sigma_x).
+// TIER: the phase tier of opD, one instantiation per tier so that each warp
+// runs straight-line code.
+template <class T, int LOGN, int LOGE, int F, int TIER>
 __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&pd)[(1 << LOGE) / 2], int t, int comp,
                                          int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T g11, T g22,
-                                         T g12, T htau, T xang, int pieces, double (&nsum)[2]) {
+                                         T g12, T htau, T xang, int pieces, bool ymerge, T tm, T sm,
+                                         double (&nsum)[2]) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
   constexpr bool IMAG = (F & F_IMAG) != 0;
+  constexpr bool MERGE = !IMAG && (F & F_REND) && (F & F_RSTART) && !(F & F_PART);
 #pragma unroll
   for (int j = 0; j < H; ++j) {
     const int x = t + (j + comp * H) * TT;
@@ -283,19 +333,27 @@ __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&p
       q2z = q.z;
     }
     const XPoint<T> xc = xpoint<IMAG, T>(px, ty, p2 != nullptr, q2z, xang);
-    if constexpr (F & F_REND) {
-      applyX<IMAG>(u, d, xc, pieces);
-      opD<IMAG, FAST>(u, d, vu, vd, g11, g22, g12, htau);
-      applyX<IMAG>(u, d, xc, pieces);
-    }
-    if constexpr (F & F_PART) {
-      nsum[0] += double(cabs2(u));
-      nsum[1] += double(cabs2(d));
-    }
-    if constexpr (F & F_RSTART) {
-      applyX<IMAG>(u, d, xc, pieces);
-      opD<IMAG, FAST>(u, d, vu, vd, g11, g22, g12, htau);
-      applyX<IMAG>(u, d, xc, pieces);
+    if constexpr (MERGE) {
+      applyX<false>(u, d, xc, pieces);
+      opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+      applyX2(u, d, xc, pieces, ymerge, tm, sm);
+      opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+      applyX<false>(u, d, xc, pieces);
+    } else {
+      if constexpr (F & F_REND) {
+        applyX<IMAG>(u, d, xc, pieces);
+        opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+        applyX<IMAG>(u, d, xc, pieces);
+      }
+      if constexpr (F & F_PART) {
+        nsum[0] += double(cabs2(u));
+        nsum[1] += double(cabs2(d));
+      }
+      if constexpr (F & F_RSTART) {
+        applyX<IMAG>(u, d, xc, pieces);
+        opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+        applyX<IMAG>(u, d, xc, pieces);
+      }
     }
   }
 }
@@ -333,22 +391,35 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     T htau, xang;
     if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
     const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
-    // One code path per warp: the small-phase series when, for every point of
-    // the warp, |htau e| stays below the series' range.  e <= Vb + G rho_tot with
-    // Vb = max |V +- delta/2| of the instance and G = max(|g11|, |g22|) + |g12|;
-    // rho_tot = |u|^2 + |d|^2 at a point is left unchanged by real-time R
-    // (5 % margin for the imaginary-time X).
+    // One phase tier per warp: the shortest series whose range holds |htau e|
+    // at every point of the warp.  e <= Vb + G rho_tot with Vb = max |V +-
+    // delta/2| of the instance and G = max(|g11|, |g22|) + |g12|; rho_tot =
+    // |u|^2 + |d|^2 at a point is left unchanged by real-time R (5 % margin
+    // for the imaginary-time X).
     T rmax = T(0);
 #pragma unroll
     for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
                                                       d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
     const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
     const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
-    const bool fast = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
-    if (fast)
-      r_points<T, LOGN, LOGE, F, true>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, nsum);
-    else
-      r_points<T, LOGN, LOGE, F, false>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, nsum);
+    const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
+    const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
+    T tm = T(0), sm = T(0);
+    bool ymerge = false;
+    if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
+#define SPGPE_R_POINTS(TIER) \
+  r_points<T, LOGN, LOGE, F, TIER>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum)
+    if constexpr (sizeof(T) == 8) {
+      SPGPE_R_POINTS(2);
+    } else {
+      if (!IMAG && tiny)  // imaginary time has no tier 0
+        SPGPE_R_POINTS(0);
+      else if (small)
+        SPGPE_R_POINTS(1);
+      else
+        SPGPE_R_POINTS(2);
+    }
+#undef SPGPE_R_POINTS
     // scatter back to one component per thread
 #pragma unroll
     for (int j = 0; j < H; ++j) {

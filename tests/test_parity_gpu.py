@@ -208,7 +208,11 @@ def test_host_spinor_path_is_bit_identical(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_split_runs_are_bit_identical(dtype):
+def test_split_runs_agree(dtype):
+    """Real time: within a call the closing X(dt/4) of one step and the opening
+    X(dt/4) of the next are applied as one rotation by the doubled angle; at a
+    call boundary they are applied one after the other, so a split run agrees
+    to rounding.  Imaginary time has no such merge: bit-identical."""
     p = coupled(64, 128)
     psi0 = inputs.gaussian_spinor(p.grid, seed=8)
     with ctx_for(p, dtype) as c:
@@ -216,7 +220,9 @@ def test_split_runs_are_bit_identical(dtype):
         c.step_real(a, 1e-3, 30)
         c.step_real(b, 1e-3, 13)
         c.step_real(b, 1e-3, 17)
-        assert torch.equal(a, b)
+        tol = 1e-13 if dtype == "c128" else 2e-6
+        assert np.abs(to_host(a) - to_host(b)).max() < tol * np.abs(to_host(a)).max()
+        b.copy_(a)
         c.step_imag(a, 1e-3, 30, sp.SPGPE_NORM_TOTAL)
         c.step_imag(b, 1e-3, 11)
         c.step_imag(b, 1e-3, 19)
