@@ -120,6 +120,32 @@ int spgpe_step_real(spgpe_ctx *ctx, void *psi, double dt, int nsteps);
 int spgpe_step_imag(spgpe_ctx *ctx, void *psi, double dtau, int nsteps, int norm_mode,
                     const double *target, double *residual_out);
 
+/* Imaginary-time relaxation to a residual tolerance (the ground-state search
+ * of Sec. 3.2 and Sec. 6, run until it has converged instead of for a fixed
+ * number of steps).  Runs spgpe_step_imag in chunks of check_every steps, each
+ * chunk ending with the discrete-map residual of its last step (defined as
+ * for spgpe_step_imag), until every instance has residual <= tol or max_steps
+ * steps have run.  dtau, norm_mode and target as for spgpe_step_imag.
+ * flags = SPGPE_RELAX_LADDER on a complex128 context first relaxes a
+ * complex64 copy of the spinor with the same model (the context's own
+ * complex64 twin, allocated on first use): rounded once, stepped in complex64
+ * until every residual is <= max(tol, handoff), or, with handoff = 0, until
+ * the residual has reached complex64's rounding floor (about 2^-24 / dtau
+ * times a modest factor) and stops improving; then widened back into psi and
+ * relaxed in complex128 to tol.  The rounding of every complex64 step also
+ * excites slowly relaxing modes that a smooth initial state leaves untouched,
+ * so the ladder pays off for initial states far from the ground state (random
+ * or vortex-seeded), and a hand-off residual well above the floor limits that
+ * noise.  The flag is ignored on complex64 contexts; handoff >= 0.
+ * residual_out (host, nullable): ninst doubles, the last residual of each
+ * instance.  steps_out (host, nullable): {steps run in complex64 by the
+ * ladder, steps run in the context's precision}.  Returns SPGPE_OK also when
+ * max_steps ran out first (compare residual_out with tol).  Synchronises. */
+enum { SPGPE_RELAX_LADDER = 1 };
+int spgpe_relax(spgpe_ctx *ctx, void *psi, double dtau, double tol, int max_steps, int check_every,
+                int norm_mode, const double *target, int flags, double handoff, double *residual_out,
+                int *steps_out);
+
 /* Energy functional whose variation is H Psi, per instance:
  * out[6*i .. 6*i+5] = {E_total, E_kinetic (incl. -kL kx sigma_z), E_trap,
  * E_detuning, E_Raman, E_interaction}, extensive (divide by the atom number

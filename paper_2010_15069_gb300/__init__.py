@@ -20,14 +20,14 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SpgpeError,
-                   check, load)
+from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SPGPE_RELAX_LADDER,
+                   SpgpeError, check, load)
 
 __all__ = [
-    "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SpgpeError",
+    "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SpgpeError",
     "Context", "load",
     "spgpe_init_grid", "spgpe_init_batch", "spgpe_set_potentials", "spgpe_set_potentials_separable",
-    "spgpe_step_real", "spgpe_step_imag", "spgpe_energy", "spgpe_norm", "spgpe_sync",
+    "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_energy", "spgpe_norm", "spgpe_sync",
     "spgpe_cufft_step_real", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
     "spgpe_last_launches", "spgpe_set_timing", "spgpe_timing",
 ]
@@ -86,6 +86,18 @@ def spgpe_step_imag(ctx, psi_ptr, dtau, nsteps, norm_mode=SPGPE_NORM_TOTAL, targ
     check(load().spgpe_step_imag(ctx, ctypes.c_void_p(int(psi_ptr)), float(dtau), int(nsteps), int(norm_mode),
                                  _ptr(tgt), _ptr(res)), ctx)
     return res
+
+
+def spgpe_relax(ctx, psi_ptr, dtau, tol, max_steps, check_every=200, norm_mode=SPGPE_NORM_TOTAL,
+                target=(0.5, 0.5), flags=0, handoff=0.0, ninst=1):
+    """Returns (residuals per instance, (steps in complex64, steps in the context's precision))."""
+    tgt = _f64(target, 2)
+    res = np.zeros(int(ninst))
+    steps = np.zeros(2, dtype=np.int32)
+    check(load().spgpe_relax(ctx, ctypes.c_void_p(int(psi_ptr)), float(dtau), float(tol), int(max_steps),
+                             int(check_every), int(norm_mode), _ptr(tgt), int(flags), float(handoff), _ptr(res),
+                             steps.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return res, (int(steps[0]), int(steps[1]))
 
 
 def spgpe_energy(ctx, psi_ptr, ninst=1):
@@ -215,6 +227,11 @@ class Context:
     def step_imag(self, psi, dtau, nsteps, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5), residual=False):
         return spgpe_step_imag(self._ctx, self._check_psi(psi), dtau, nsteps, norm_mode, target,
                                residual, self.ninst)
+
+    def relax(self, psi, dtau, tol, max_steps, check_every=200, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5),
+              ladder=False, handoff=0.0):
+        return spgpe_relax(self._ctx, self._check_psi(psi), dtau, tol, max_steps, check_every, norm_mode, target,
+                           SPGPE_RELAX_LADDER if ladder else 0, handoff, self.ninst)
 
     def cufft_step_real(self, psi, dt, nsteps):
         spgpe_cufft_step_real(self._ctx, self._check_psi(psi), dt, nsteps)

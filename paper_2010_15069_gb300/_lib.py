@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspgpe.so")
 
 SPGPE_C64, SPGPE_C128 = 1, 2
 SPGPE_NORM_TOTAL, SPGPE_NORM_PER_COMPONENT = 0, 1
+SPGPE_RELAX_LADDER = 1
 STATUS = {0: "SPGPE_OK", -1: "SPGPE_EINVAL", -2: "SPGPE_ENOMEM", -3: "SPGPE_ECUDA",
           -4: "SPGPE_ENONFINITE", -5: "SPGPE_ETIMEOUT", -6: "SPGPE_ESTATE"}
 
@@ -37,6 +38,7 @@ SIGNATURES = {
     "spgpe_set_timing": (_I, [_P, _I]),
     "spgpe_timing": (_I, [_P, _P, _P]),
     "spgpe_norm_noalloc": (_I, [_P, _I, _I, _I, _D, _D, _I, _P, _P]),
+    "spgpe_relax": (_I, [_P, _P, _D, _D, _I, _I, _I, _P, _I, _D, _P, _P]),
 }
 NKINDS = 9
 KIND_NAMES = ["row_real_open", "row_real_fused", "row_real_close", "col_real", "row_imag_open",

@@ -40,7 +40,8 @@ struct spgpe_ctx {
   bool has2d = false;
 
   // Device tables.
-  void *d_twx = nullptr, *d_twy = nullptr;
+  void *d_twx = nullptr, *d_twy = nullptr;  // twiddle tables: row plan (x), column plan (y)
+  void *d_twe = nullptr;                     // energy-row plan (x), when it differs from the row plan
   void *d_tabx = nullptr, *d_taby = nullptr;  // step tables for (tab_dt, tab_imag)
   void *d_rawx = nullptr, *d_rawy = nullptr;  // raw (V, delta, Omega) for energies
   void *d_pot2d = nullptr;
@@ -57,6 +58,14 @@ struct spgpe_ctx {
   int tab_imag = -1;
   int omega_pieces = 0;
   double vbound2d = 0.0;  // max |V +- delta/2| of the 2D arrays (0 when separable)
+  std::vector<double> h2d;  // host copy of the 2D {V + delta/2, V - delta/2, Omega, 0} table
+  unsigned model_version = 0;
+
+  // Precision ladder (spgpe_relax): a complex64 twin of a complex128 context
+  // with the same model, and its spinor buffer.
+  spgpe_ctx *twin = nullptr;
+  unsigned twin_version = ~0u;
+  void *d_psi64 = nullptr;
 
   cufftHandle plan = 0;
   bool plan_ok = false;
@@ -64,7 +73,7 @@ struct spgpe_ctx {
   // Persistent passes: multiprocessor count, and the column tensor map of the
   // spinor buffer last stepped (rebuilt when the buffer changes).
   int sms = 0;
-  bool persistent_row = false;  // the row pass is arithmetic-bound: the plain pass is faster
+  bool persistent_row = true;
   bool persistent_col = true;
   const void *map_psi = nullptr;
   CUtensorMap map{};
@@ -137,44 +146,62 @@ void free_all(spgpe_ctx *c) {
     cudaEventDestroy(u.second.second);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  void *ps[] = {c->d_twx, c->d_twy, c->d_tabx, c->d_taby, c->d_rawx, c->d_rawy, c->d_pot2d, c->d_kxt,
+  void *ps[] = {c->d_twx, c->d_twy, c->d_twe, c->d_tabx, c->d_taby, c->d_rawx, c->d_rawy, c->d_pot2d, c->d_kxt,
                 c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_flags, c->d_scratch,
                 c->d_stage};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (c->plan_ok) cufftDestroy(c->plan);
+  if (c->d_psi64) cudaFree(c->d_psi64);
+  if (c->twin) {
+    free_all(c->twin);
+    delete c->twin;
+  }
 }
 
-// Forward roots exp(-2 pi i m / n) for the single-precision transforms, as
-// (tan(phi/2), sin(phi)) with exp(-2 pi i m / n) = g exp(i phi), g = +-1,
-// phi in [-pi/2, pi/2]; the kernels rotate by phi with three shears
-// (determinant one whatever the rounding) and negate exactly where g = -1
-// (n/4 < m < 3n/4, recomputed from m).
-std::vector<float> roots_f32(int n) {
-  std::vector<float> w(2 * (size_t)n);
-  for (int m = 0; m < n; ++m) {
-    double th = -kTwoPi * m / n;                 // (-2 pi, 0]
-    if (th <= -0.5 * kTwoPi) th += kTwoPi;       // (-pi, pi]
-    double g = 1.0, phi = th;
-    if (std::fabs(th) > 0.25 * kTwoPi) {         // left half plane: rotate by th -+ pi, negate
-      g = -1.0;
-      phi = th > 0 ? th - 0.5 * kTwoPi : th + 0.5 * kTwoPi;
+// Twiddle table of the block FFT plan for n = 2^logn points with 2^loge
+// values per thread (the plan of fft_core.cuh: S = ceil(logn / loge) stages,
+// radix bits split as evenly as possible, larger first).  Stage s >= 1 holds
+// entries [r - 1][k], r = 1..R-1, k = 0..NS-1, for the root exp(-2 pi i m / n),
+// m = r k n / (NS R); 16 bytes per entry:
+//   complex64:  (tan(phi/2), sin(phi), g, 0) with exp(-2 pi i m / n) = g e^{i phi},
+//               g = +-1, phi in [-pi/2, pi/2] (three-shear rotation, exact sign);
+//   complex128: (cos, -sin) of 2 pi m / n.
+std::vector<double> stage_twiddles(int logn, int loge, bool single) {
+  const int n = 1 << logn;
+  const int S = (logn + loge - 1) / loge;
+  std::vector<double> out;
+  int ns = 1;
+  for (int s = 0; s < S; ++s) {
+    const int bits = logn / S + (s < logn % S ? 1 : 0), R = 1 << bits;
+    if (s > 0) {
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < ns; ++k) {
+          const long m = (long)r * k * (n / (ns * R));
+          if (single) {
+            double th = -kTwoPi * (double)m / n;      // (-2 pi, 0]
+            if (th <= -0.5 * kTwoPi) th += kTwoPi;    // (-pi, pi]
+            double g = 1.0, phi = th;
+            if (std::fabs(th) > 0.25 * kTwoPi) {      // left half plane: rotate by th -+ pi, negate
+              g = -1.0;
+              phi = th > 0 ? th - 0.5 * kTwoPi : th + 0.5 * kTwoPi;
+            }
+            out.insert(out.end(), {std::tan(0.5 * phi), std::sin(phi), g, 0.0});
+          } else {
+            out.insert(out.end(), {std::cos(kTwoPi * (double)m / n), -std::sin(kTwoPi * (double)m / n)});
+          }
+        }
     }
-    (void)g;
-    w[2 * m] = (float)std::tan(0.5 * phi);
-    w[2 * m + 1] = (float)std::sin(phi);
+    ns *= R;
   }
-  return w;
+  if (out.empty()) out.assign(single ? 4 : 2, 0.0);  // one-stage plans read no twiddle
+  return out;
 }
 
-// Forward roots exp(-2 pi i m / n), FP64.
-std::vector<double> roots(int n) {
-  std::vector<double> w(2 * (size_t)n);
-  for (int m = 0; m < n; ++m) {
-    w[2 * m] = std::cos(kTwoPi * m / n);
-    w[2 * m + 1] = -std::sin(kTwoPi * m / n);
-  }
-  return w;
+int log2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
 }
 
 double kval(int i, int n, double d) { return kTwoPi * (i < n / 2 ? i : i - n) / (n * d); }
@@ -522,8 +549,7 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
   // (6 per row block + 2 per column block), norms (256 blocks of 2)
   c->n_partials = (size_t)ninst * (6 * (size_t)ny + 2 * (size_t)nx + 2 * 1024);
   int r;
-  if ((r = dev_alloc(c, &c->d_twx, (size_t)nx * 16)) || (r = dev_alloc(c, &c->d_twy, (size_t)ny * 16)) ||
-      (r = dev_alloc(c, &c->d_tabx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_taby, (size_t)ninst * ny * q)) ||
+  if ((r = dev_alloc(c, &c->d_tabx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_taby, (size_t)ninst * ny * q)) ||
       (r = dev_alloc(c, &c->d_rawx, (size_t)ninst * nx * q)) || (r = dev_alloc(c, &c->d_rawy, (size_t)ninst * ny * q)) ||
       (r = dev_alloc(c, &c->d_kxt, (size_t)ninst * 2 * nx * es)) || (r = dev_alloc(c, &c->d_kyt, ny * es)) ||
       (r = dev_alloc(c, (void **)&c->d_gpar, (size_t)ninst * 4 * sizeof(double))) ||
@@ -551,22 +577,25 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
       c->sms = 0;
     cudaGetLastError();
     // SPGPE_PERSISTENT selects the pass variants: 0 plain passes, 1 persistent
-    // column pass (default), 2 persistent row and column passes.
+    // column pass only, 2 persistent row and column passes (default).
     const char *env = std::getenv("SPGPE_PERSISTENT");
     if (env && env[0] >= '0' && env[0] <= '2') {
       c->persistent_col = env[0] != '0';
       c->persistent_row = env[0] == '2';
     }
   }
-  if (dtype == SPGPE_C64) {
-    const std::vector<float> wx = roots_f32(nx), wy = roots_f32(ny);
-    if (cudaMemcpyAsync(c->d_twx, wx.data(), wx.size() * sizeof(float), cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_twy, wy.data(), wy.size() * sizeof(float), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
-      r = SPGPE_ECUDA, c->err = "twiddle upload failed";
-    else
-      r = SPGPE_OK;
-  } else if (!(r = upload(c, c->d_twx, roots(nx)))) {
-    r = upload(c, c->d_twy, roots(ny));
+  {
+    const int lx = log2i(nx), ly = log2i(ny), esz = (int)es;
+    const bool single = dtype == SPGPE_C64;
+    const std::vector<double> wr = stage_twiddles(lx, row_loge_for(lx, esz), single);
+    const std::vector<double> wc = stage_twiddles(ly, col_loge_for(ly, esz), single);
+    const bool sep_e = erow_loge_for(lx, esz) != row_loge_for(lx, esz);
+    const std::vector<double> we = sep_e ? stage_twiddles(lx, erow_loge_for(lx, esz), single) : std::vector<double>();
+    auto put = [&](void **d, const std::vector<double> &w) -> int {
+      int rr = dev_alloc(c, d, w.size() * (single ? sizeof(float) : sizeof(double)));
+      return rr ? rr : upload(c, *d, w);
+    };
+    if (!(r = put(&c->d_twx, wr)) && !(r = put(&c->d_twy, wc)) && sep_e) r = put(&c->d_twe, we);
   }
   if (r) {
     g_init_error = c->err;
@@ -630,6 +659,8 @@ int spgpe_set_potentials(spgpe_ctx *c, const double *V, const double *delta, con
   if (r) return r;
   if ((r = upload(c, c->d_pot2d, p2))) return r;
   c->has2d = true;
+  c->h2d.swap(p2);
+  ++c->model_version;
   if ((r = upload_raw(c))) return r;
   CK(c, cudaStreamSynchronize(c->st));
   std::fill(c->inst_set.begin(), c->inst_set.end(), 1);
@@ -647,10 +678,12 @@ int spgpe_set_potentials_separable(spgpe_ctx *c, int inst, const double *Vx, con
     return fail(c, SPGPE_EINVAL, "potential pieces must be finite");
   const double g[4] = {g11, g22, g12, kL};
   if (!all_finite(g, 4)) return fail(c, SPGPE_EINVAL, "couplings must be finite");
+  ++c->model_version;
   if (c->has2d) {
     // a separable call replaces the 2D model for every instance
     c->has2d = false;
     c->vbound2d = 0.0;
+    c->h2d.clear();
     if (inst >= 0) std::fill(c->inst_set.begin(), c->inst_set.end(), 0);
   }
   const int i0 = inst < 0 ? 0 : inst, i1 = inst < 0 ? c->ninst : inst + 1;
@@ -831,7 +864,7 @@ int spgpe_energy(spgpe_ctx *c, const void *psi, double *out) {
   a.rawx = c->d_rawx;
   a.rawy = c->d_rawy;
   a.pot2d = c->has2d ? c->d_pot2d : nullptr;
-  a.twx = c->d_twx;
+  a.twx = c->d_twe ? c->d_twe : c->d_twx;
   a.twy = c->d_twy;
   a.gpar = c->d_gpar;
   a.partials = c->d_partials;
@@ -909,3 +942,109 @@ int spgpe_cufft_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ relaxation to a tolerance
+
+namespace {
+
+// The complex64 twin of a complex128 context (same grid, batch, stream and
+// model) and its spinor buffer, brought up to date with the model.
+int ensure_twin(spgpe_ctx *c) {
+  if (!c->twin) {
+    spgpe_ctx *t = nullptr;
+    const int r = init_common(&t, c->nx, c->ny, c->xmax, c->ymax, c->ninst, SPGPE_C64, c->st);
+    if (r) return fail(c, r, "complex64 twin: " + g_init_error);
+    t->persistent_row = c->persistent_row;
+    t->persistent_col = c->persistent_col;
+    c->twin = t;
+  }
+  spgpe_ctx *t = c->twin;
+  if (c->twin_version != c->model_version) {
+    t->hx = c->hx;
+    t->hy = c->hy;
+    t->hg = c->hg;
+    t->inst_set = c->inst_set;
+    t->has2d = c->has2d;
+    t->vbound2d = c->vbound2d;
+    t->h2d = c->h2d;
+    int r = SPGPE_OK;
+    if (t->has2d) {
+      if ((r = dev_alloc(t, &t->d_pot2d, (size_t)c->nx * c->ny * 2 * t->es)) || (r = upload(t, t->d_pot2d, t->h2d)))
+        return fail(c, r, "complex64 twin: " + t->err);
+    }
+    if ((r = upload_raw(t))) return fail(c, r, "complex64 twin: " + t->err);
+    c->twin_version = c->model_version;
+  }
+  return dev_alloc(c, &c->d_psi64, t->psi_bytes());
+}
+
+// Imaginary-time steps in chunks of `check`, each ending with the residual of
+// its last step, until every instance is within tol or max_steps have run.
+// to_floor: also stop once the largest residual has reached the rounding
+// floor of complex64 (below 2^-18 / dtau) and improves by less than a fifth
+// from one chunk to the next.
+int relax_stage(spgpe_ctx *c, void *p, double dtau, double tol, int max_steps, int check, int norm_mode,
+                const double *target, bool to_floor, std::vector<double> &res, int *steps, int *launches) {
+  const double floor64 = std::ldexp(1.0, -18) / dtau;
+  double prev = INFINITY;
+  int done = 0;
+  while (done < max_steps) {
+    const int n = std::min(check, max_steps - done);
+    const int r = spgpe_step_imag(c, p, dtau, n, norm_mode, target, res.data());
+    if (r) return r;
+    *launches += c->last_launches;
+    done += n;
+    double rmax = 0.0;
+    for (double v : res) rmax = std::isnan(v) ? INFINITY : std::max(rmax, v);
+    if (rmax <= tol) break;
+    if (to_floor && rmax < floor64 && rmax > 0.8 * prev) break;
+    prev = rmax;
+  }
+  *steps = done;
+  return SPGPE_OK;
+}
+
+}  // namespace
+
+extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int max_steps, int check_every,
+                           int norm_mode, const double *target, int flags, double handoff, double *residual_out,
+                           int *steps_out) {
+  int r = check_ready(c);
+  if (r) return r;
+  c->last_launches = 0;
+  if (!psi || !(dtau > 0) || !std::isfinite(dtau) || !(tol > 0) || max_steps < 1 || check_every < 1 ||
+      !(handoff >= 0) || !std::isfinite(handoff))
+    return fail(c, SPGPE_EINVAL, "bad psi, dtau, tol, max_steps, check_every or handoff");
+  if (flags & ~SPGPE_RELAX_LADDER) return fail(c, SPGPE_EINVAL, "unknown flags");
+  const bool ladder = (flags & SPGPE_RELAX_LADDER) && c->dtype == SPGPE_C128;
+  void *p;
+  bool host;
+  if ((r = begin_psi(c, psi, &p, &host))) return r;
+  std::vector<double> res((size_t)c->ninst, NAN);
+  int s64 = 0, s = 0, launches = 0;
+  if (ladder) {
+    if ((r = ensure_twin(c))) return r;
+    const long n = (long)c->ninst * 2 * c->plane();
+    CK(c, launch_convert(p, 16, c->d_psi64, 8, n, c->sms, c->st));
+    // complex64 down to the hand-off residual, or (handoff = 0) its rounding floor
+    r = relax_stage(c->twin, c->d_psi64, dtau, std::max(tol, handoff), max_steps, check_every, norm_mode, target,
+                    handoff == 0.0, res, &s64, &launches);
+    if (r) return fail(c, r, "complex64 stage: " + c->twin->err);
+    CK(c, launch_convert(c->d_psi64, 8, p, 16, n, c->sms, c->st));
+    launches += 2;
+  }
+  if (max_steps - s64 >= 1) {
+    // a context's own steps; the staged host spinor is already on the device
+    r = relax_stage(c, p, dtau, tol, max_steps - s64, check_every, norm_mode, target, false, res, &s, &launches);
+    if (r) return r;
+  }
+  c->last_launches = launches;
+  if ((r = end_psi(c, psi, host))) return r;
+  if (residual_out)
+    for (int i = 0; i < c->ninst; ++i) residual_out[i] = res[(size_t)i];
+  if (steps_out) {
+    steps_out[0] = s64;
+    steps_out[1] = s;
+  }
+  return SPGPE_OK;
+}

@@ -76,25 +76,28 @@ __device__ __forceinline__ cx<T> w16(cx<T> a) {
   }
 }
 
-// Stage twiddles.  Double precision: the root exp(-2 pi i m / N) as a complex
-// pair.  Single precision: exp(-2 pi i m / N) = g R(phi) with g = +-1 and
-// R(phi) a rotation by phi in [-pi/2, pi/2], stored as (tan(phi/2), sin(phi))
-// and applied with three shears; g = -1 exactly for N/4 < m < 3N/4 and is
-// recomputed from m.  A single-precision (cos, sin) pair is off unit modulus
+// Stage twiddles, one table per transform plan, laid out per stage as
+// [r - 1][k] (r = 1..R-1 the butterfly input, k = 0..NS-1 its position within
+// the previous span), so that the threads of a warp read consecutive entries
+// and every read has a compile-time offset; entry (r, k) of a stage is the
+// forward root exp(-2 pi i m / N) with m = r k N / (NS R).
+// Double precision: the root as a complex pair.  Single precision: the root
+// is g R(phi) with g = +-1 and R(phi) a rotation by phi in [-pi/2, pi/2],
+// stored as (tan(phi/2), sin(phi), g, 0) and applied with three shears and a
+// multiplication by g.  A single-precision (cos, sin) pair is off unit modulus
 // by about 2^-25 in a direction that does not average out over the set of
 // roots; every element passes through these factors in every transform, and
 // rounded pairs drain the norm by about 1e-7 per forward/inverse round trip.
 template <class T> struct TwType;
-template <> struct TwType<float> { using type = float2; };
+template <> struct TwType<float> { using type = float4; };
 template <> struct TwType<double> { using type = cx<double>; };
 
-template <int N, int SIGN, class T>
-__device__ __forceinline__ cx<T> twiddle(cx<T> u, const typename TwType<T>::type &w, int m) {
+template <int SIGN, class T>
+__device__ __forceinline__ cx<T> twiddle(cx<T> u, const typename TwType<T>::type &w) {
   if constexpr (sizeof(T) == 4) {
     const float t = SIGN < 0 ? w.x : -w.x, s = SIGN < 0 ? w.y : -w.y;  // inverse: R(-phi)
     const cx<T> r = shear_rot(u, t, s);
-    const bool neg = (unsigned)(4 * m - N - 1) < (unsigned)(2 * N - 1);
-    return {neg ? -r.re : r.re, neg ? -r.im : r.im};
+    return {r.re * w.z, r.im * w.z};
   } else {
     const cx<T> c = SIGN < 0 ? w : cx<T>{w.re, -w.im};
     return cmul(u, c);
@@ -151,10 +154,15 @@ struct Plan {
   static constexpr int S = (LOGN + LOGE - 1) / LOGE;
   __host__ __device__ static constexpr int bits(int s) { return LOGN / S + (s < LOGN % S ? 1 : 0); }
   __host__ __device__ static constexpr int nsbits(int s) { return s == 0 ? 0 : nsbits(s - 1) + bits(s - 1); }
+  // offset of stage s in the twiddle table (stage 0 has none)
+  __host__ __device__ static constexpr int off(int s) {
+    return s <= 1 ? 0 : off(s - 1) + ((1 << bits(s - 1)) - 1) * (1 << nsbits(s - 1));
+  }
+  __host__ __device__ static constexpr int entries() { return off(S); }
 };
 
 // One Stockham stage over NSEQ sequences.  Acc maps (sequence, position) to a
-// shared-memory slot; tw[m] encodes the forward root exp(-2 pi i m / N).
+// shared-memory slot; tw is this stage's part of the twiddle table.
 template <int N, int E, int R, int NS, bool LAST, int SIGN, int NSEQ, class T, class Acc>
 __device__ __forceinline__ void fft_stage(cx<T> (&v)[NSEQ][E], int t,
                                           const typename TwType<T>::type *__restrict__ tw, const Acc &acc) {
@@ -171,10 +179,7 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[NSEQ][E], int t,
       for (int r = 0; r < R; ++r) u[r] = v[q][b + r * B];
       if constexpr (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const int m = (r * k) * (N / (NS * R));
-          u[r] = twiddle<N, SIGN, T>(u[r], tw[m], m);
-        }
+        for (int r = 1; r < R; ++r) u[r] = twiddle<SIGN, T>(u[r], tw[(r - 1) * NS + k]);
       }
       dft<R, SIGN>(u);
       if constexpr (LAST) {
@@ -198,7 +203,7 @@ __device__ __forceinline__ void fft_stages(cx<T> (&v)[NSEQ][1 << LOGE], int t,
     constexpr int R = 1 << P::bits(STAGE);
     constexpr int NS = 1 << P::nsbits(STAGE);
     constexpr bool LAST = (STAGE == P::S - 1);
-    fft_stage<N, E, R, NS, LAST, SIGN, NSEQ>(v, t, tw, acc);
+    fft_stage<N, E, R, NS, LAST, SIGN, NSEQ>(v, t, tw + P::off(STAGE), acc);
     if constexpr (!LAST) {
       acc.sync();
 #pragma unroll
@@ -211,7 +216,8 @@ __device__ __forceinline__ void fft_stages(cx<T> (&v)[NSEQ][1 << LOGE], int t,
   }
 }
 
-// Length-2^LOGN transform of NSEQ sequences held as described above.
+// Length-2^LOGN transform of NSEQ sequences held as described above; tw_table
+// is the plan's twiddle table (Plan<LOGN, LOGE>::entries() entries).
 // SIGN = -1 forward (unnormalised), +1 inverse (unnormalised).  Must be called
 // by every thread that acc.sync() synchronises (the block, or the warp when
 // all exchange partners of a sequence share a warp).

@@ -32,7 +32,7 @@ struct RowArgs {
                           // X constants: (tan(a/2), sin a) in real time, (cosh a - 1, sinh a)
                           // in imaginary time, a = Omega piece * dt / 8
   const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
-  const void *tw;         // [nx] forward roots (see TwType in fft_core.cuh)
+  const void *tw;         // twiddle table of the x plan (see TwType in fft_core.cuh)
   const double *gpar;     // [ninst][4] {g11, g22, g12, kL}
   const void *gparT;      // the same in the working precision
   double tau;             // D substep (dt/2)
@@ -40,7 +40,6 @@ struct RowArgs {
   double htau_d;          // -tau/2 (real time, half phase) or -tau (imaginary time)
   float htau_f;           // the same in single precision
   float xang_f;           // xang in single precision
-  int tab_in_smem;        // persistent pass: x step table copied with each tile
   int omega_pieces;       // bit 0: some Omega_y != 0, bit 1: some Omega_x != 0 (separable pieces)
   double *partials;       // [ninst][gridDim.x][2]
   unsigned *counters;     // [ninst], zero between launches
@@ -60,7 +59,7 @@ struct ColArgs {
   int *flags;             // error bits (persistent pass: bit 1 = transfer wait timed out)
   const void *kxt;        // [ninst][2][nx] complex a_j(kx) - 1
   const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
-  const void *tw;         // [ny] forward roots (see TwType in fft_core.cuh)
+  const void *tw;         // twiddle table of the y plan (see TwType in fft_core.cuh)
   int nx, ny, ninst, C;
 };
 
@@ -71,7 +70,7 @@ struct EnergyArgs {
   const void *rawx;       // [ninst][nx] {Vx, delta_x, Omega_x, 0}
   const void *rawy;       // [ninst][ny] {Vy, delta_y, Omega_y, 0}
   const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
-  const void *twx, *twy;
+  const void *twx, *twy;  // twiddle tables of the energy-row x plan and the column y plan
   const double *gpar;
   double *partials;       // row pass: [ninst][gridDim.x][6]; column pass: [ninst][2][gridDim.x]
   double dkx, dky;        // 2 pi / (n d)
@@ -91,6 +90,20 @@ __host__ __device__ constexpr int row_stride(int n, int elem_bytes) { return 2 *
 __host__ __device__ constexpr int col_smem_elems(int n, int c, int elem_bytes) {
   return n * c + ((n * c) >> pad_shift(elem_bytes)) + 1;
 }
+
+// log2 of the values each thread holds in the block FFTs (one component per
+// thread).  Row pass: 16 complex64 or 8 complex128, 16 complex128 at 4096 so
+// that one row fits a 512-thread block.  Column pass: the same, with 16
+// complex128 from 2048 up.  Energy row pass (two components per thread):
+// 16 complex64, 8 complex128.
+__host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int row_loge_for(int logn, int es) {
+  return es == 8 ? imin(logn, 4) : (logn >= 12 ? 4 : imin(logn, 3));
+}
+__host__ __device__ constexpr int col_loge_for(int logn, int es) {
+  return es == 8 ? imin(logn, 4) : (logn >= 11 ? 4 : imin(logn, 3));
+}
+__host__ __device__ constexpr int erow_loge_for(int logn, int es) { return imin(logn, es == 8 ? 4 : 3); }
 
 // Launch geometry of the fused passes (host and device agree on it).
 struct LaunchShape {
@@ -115,12 +128,17 @@ template <class T> cudaError_t launch_residual(const void *psi, const void *prev
                                                double *partials, int blocks, cudaStream_t s);
 template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStream_t s);
 // Persistent passes (async tile loads; psi must be 16-byte aligned).  sms is
-// the device's multiprocessor count; the column pass reads psi through `map`,
+// the device's multiprocessor count.  They return cudaErrorNotSupported for
+// shapes they do not cover (the caller then runs the plain pass).  The
+// column pass reads psi through `map`,
 // a 2D tensor map over [ninst*2*ny rows][nx complex] with a box of
 // colp_cols<T>() columns by min(ny, 256) rows.
 template <class T> cudaError_t launch_row_p(int flags, RowArgs a, cudaStream_t s, int sms);
 template <class T> int colp_cols(int nx, int ny);
 template <class T> cudaError_t launch_col_p(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t s, int sms);
 template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t s);
+// Round complex128 to complex64 (src_es 16, dst_es 8) or widen complex64 to
+// complex128 (8, 16): n complex values, grid of at most 8 blocks per SM.
+cudaError_t launch_convert(const void *src, int src_es, void *dst, int dst_es, long n, int sms, cudaStream_t s);
 
 }  // namespace spgpe

@@ -35,84 +35,206 @@ __device__ __forceinline__ void drain_after_timeout(uint64_t *bar, int i, int ti
   }
 }
 
-// Shared-memory plan of the persistent row pass (host and device agree).
-__host__ __device__ constexpr size_t rowp_buf_bytes(int n, int rows, int es, bool with_tab) {
-  // exchange / dense tile region, then the x step table (n q4 = n * 2 * es bytes)
-  return (((size_t)rows * row_stride(n, es) * es + (with_tab ? (size_t)n * 2 * es : 0)) + 127) / 128 * 128;
+// ------------------------------------------------ persistent row pass
+//
+// The rows are handed out in units: a warp's worth of rows when a row lies
+// within one warp (2*TT <= 32 threads), else one row per block.  Each unit
+// owns a staging buffer, an exchange area and an mbarrier in shared memory and
+// loops over its rows; while it transforms one group of rows, the next group
+// is already streaming into its staging buffer (two bulk copies, one per
+// component, issued by the unit's first thread).  A warp unit synchronises
+// with warp barriers only, so the warps of a block never wait for one another.
+
+template <int N, int E> struct RowUnit {
+  static constexpr int TT = N / E;
+  static constexpr bool WARP = row_warp_local(TT);
+  static constexpr int ROWS = WARP ? 32 / (2 * TT) : 1;      // rows per unit
+  static constexpr int THREADS = WARP ? 32 : 2 * TT;         // threads per unit
+};
+
+// Shared-memory bytes of one unit: staging (rows x 2 components x n), then
+// the exchange area (rows x row_stride), then the mbarrier; 128-byte aligned.
+__host__ __device__ constexpr size_t rowu_bytes(int n, int rows, int es) {
+  return ((size_t)rows * 2 * n * es + (size_t)rows * row_stride(n, es) * es + 8 + 127) / 128 * 128;
+}
+
+// Atom-number partials of one warp unit (its rows belong to one instance);
+// the last unit of the instance reduces them in a fixed order and writes the
+// renormalisation scale, as row_partials does for blocks.
+__device__ __forceinline__ void warp_partials(const RowArgs &a, int inst, int group, int ngroups,
+                                              double (&nsum)[2]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nsum[0] += __shfl_xor_sync(0xffffffffu, nsum[0], o);
+    nsum[1] += __shfl_xor_sync(0xffffffffu, nsum[1], o);
+  }
+  unsigned prev = 0;
+  if (lane == 0) {
+    a.partials[((long)inst * ngroups + group) * 2] = nsum[0];
+    a.partials[((long)inst * ngroups + group) * 2 + 1] = nsum[1];
+    __threadfence();
+    prev = atomicAdd(&a.counters[inst], 1u);
+  }
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != (unsigned)ngroups - 1u) return;
+  __threadfence();
+  double tot[2] = {0.0, 0.0};
+  for (int b = lane; b < ngroups; b += 32) {
+    tot[0] += __ldcg(&a.partials[((long)inst * ngroups + b) * 2]);
+    tot[1] += __ldcg(&a.partials[((long)inst * ngroups + b) * 2 + 1]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot[0] += __shfl_xor_sync(0xffffffffu, tot[0], o);
+    tot[1] += __shfl_xor_sync(0xffffffffu, tot[1], o);
+  }
+  if (lane == 0) {
+    const double nu = tot[0] * a.wgt, nd = tot[1] * a.wgt;
+    double s0, s1;
+    if (a.norm_mode == 1) {
+      s0 = sqrt(a.tgt0 / nu);
+      s1 = sqrt(a.tgt1 / nd);
+    } else {
+      s0 = s1 = sqrt((a.tgt0 + a.tgt1) / (nu + nd));
+    }
+    if (!isfinite(s0) || !isfinite(s1)) atomicOr(a.flags, 1);
+    a.scale[2 * inst] = s0;
+    a.scale[2 * inst + 1] = s1;
+    a.counters[inst] = 0u;
+  }
+}
+
+// Warp units: blocks of SPGPE_ROWU_WARPS warps, SPGPE_ROWU_MINB of them
+// resident per SM (the register budget; 8 x 3 measured fastest on GB300 at
+// 256^2, ahead of 4 x 5, 10 x 2 and 20 x 1, and ahead of variants whose warps
+// meet at a block barrier before every row group).  Otherwise one row of
+// 2*TT threads per block.
+#ifndef SPGPE_ROWU_WARPS
+#define SPGPE_ROWU_WARPS 8
+#endif
+#ifndef SPGPE_ROWU_MINB
+#define SPGPE_ROWU_MINB 3
+#endif
+__host__ __device__ constexpr int rowu_block(int n, int e) {
+  return row_warp_local(n / e) ? 32 * SPGPE_ROWU_WARPS : 2 * (n / e);
+}
+// Dynamic shared memory of a block: its units, then (warp units only) a copy
+// of the x plan's twiddle table.
+__host__ __device__ constexpr size_t rowu_smem(int n, int e, int es, int tw_entries) {
+  return row_warp_local(n / e) ? (size_t)(rowu_block(n, e) / 32) * rowu_bytes(n, 32 / (2 * (n / e)), es) +
+                                     (size_t)tw_entries * 16
+                               : rowu_bytes(n, 1, es);
+}
+// Resident blocks the register budget is sized for: 24 warps per SM in single
+// precision, 16 in double precision.
+__host__ __device__ constexpr int rowu_min_blocks(int n, int e, int es) {
+  return row_warp_local(n / e) && es == 8 ? SPGPE_ROWU_MINB
+         : (es == 8 ? 640 : 512) / rowu_block(n, e) > 0 ? (es == 8 ? 640 : 512) / rowu_block(n, e)
+                                                         : 1;
 }
 
 template <class T, int LOGN, int LOGE, int F>
-__global__ void __launch_bounds__(2 * kRowMaxThreads) row_pass_p(const RowArgs a, int ntiles) {
+__global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
+                                  rowu_min_blocks(1 << LOGN, 1 << LOGE, sizeof(cx<T>)))
+    row_pass_p(const RowArgs a, int nunits) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
   constexpr int ES = sizeof(cx<T>);
-  constexpr int PADN = row_pad_n(N, ES), RS = row_stride(N, ES);
-  constexpr bool NEEDTAB = (F & (F_REND | F_RSTART)) != 0;
+  using U = RowUnit<N, E>;
+  constexpr int RU = U::ROWS, PADN = row_pad_n(N, ES), RS = row_stride(N, ES);
+  constexpr size_t UB = rowu_bytes(N, RU, ES);
+  constexpr uint32_t CB = (uint32_t)RU * N * ES;  // bytes of one component of a unit
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int rows = a.rows;
-  const bool tab_smem = NEEDTAB && a.tab_in_smem;
-  const size_t bufb = rowp_buf_bytes(N, rows, ES, tab_smem);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + kPipe * bufb);
-  const RowPlace pl = row_place<TT>();
-  const int groups = a.ny / rows;  // tiles per instance
-  const uint32_t rowbytes = (uint32_t)rows * N * ES;
-
-  auto buf = [&](int s) { return reinterpret_cast<cx<T> *>(smem_raw + s * bufb); };
-  auto issue = [&](int tile, int s) {
-    const int inst = tile / groups, y0 = (tile - inst * groups) * rows;
+  // Placement (as row_place, with blockDim >= 32 known here): lanes 0-15 of a
+  // warp hold component up, lanes 16-31 component down.
+  const int tx = threadIdx.x;
+  const int comp = (tx >> 4) & 1;
+  const int tp = (tx & 15) + 16 * (tx >> 5);
+  const int slot = U::WARP ? (tx >> 5) : 0;
+  const int lrow = tp / TT - slot * RU;  // row within the unit
+  const int t = tp % TT;
+  const int units_per_block = U::WARP ? (int)(blockDim.x >> 5) : 1;
+  unsigned char *ub = smem_raw + slot * UB;
+  cx<T> *stage = reinterpret_cast<cx<T> *>(ub);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ub + UB - 8);
+  const bool leader = U::WARP ? (tx & 31) == 0 : tx == 0;
+  const int upi = a.ny / RU;  // units per instance
+  auto sync_unit = [&] {
+    if constexpr (U::WARP) __syncwarp(); else __syncthreads();
+  };
+  auto issue = [&](int u) {
+    const int inst = u / upi, y0 = (u - inst * upi) * RU;
     const cx<T> *src = reinterpret_cast<const cx<T> *>(a.psi) + ((long)inst * 2 * a.ny + y0) * N;
-    const uint32_t tabbytes = tab_smem ? (uint32_t)(N * sizeof(q4<T>)) : 0u;
-    mbar_expect_tx(&bar[s], 2 * rowbytes + tabbytes);
-    bulk_g2s(buf(s), src, rowbytes, &bar[s]);
-    bulk_g2s(buf(s) + rows * N, src + (long)a.ny * N, rowbytes, &bar[s]);
-    if (tab_smem)
-      bulk_g2s(reinterpret_cast<unsigned char *>(buf(s)) + (size_t)rows * RS * ES,
-               reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N, tabbytes, &bar[s]);
+    mbar_expect_tx(bar, 2 * CB);
+    bulk_g2s(stage, src, CB, bar);
+    bulk_g2s(stage + RU * N, src + (long)a.ny * N, CB, bar);
   };
 
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kPipe; ++s) mbar_init(&bar[s], 1);
-    mbar_fence_init();
-    for (int s = 0; s < kPipe; ++s)
-      if (blockIdx.x + s * gridDim.x < ntiles) issue(blockIdx.x + s * gridDim.x, s);
+  // warp units read the twiddles from a shared-memory copy of the table
+  using TwT = typename TwType<T>::type;
+  constexpr int TWN = Plan<LOGN, LOGE>::entries();
+  const TwT *tw = reinterpret_cast<const TwT *>(a.tw);
+  if constexpr (U::WARP) {
+    TwT *tws = reinterpret_cast<TwT *>(smem_raw + units_per_block * UB);
+    for (int k = tx; k < TWN; k += blockDim.x) tws[k] = tw[k];
+    __syncthreads();
+    tw = tws;
   }
-  __syncthreads();
+  RowArgs ac = a;
+  ac.tw = tw;
 
-  int i = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
-    const int s = i % kPipe;
-    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / kPipe) & 1));
-    if (!__syncthreads_and(ok)) {
-      drain_after_timeout(bar, i, tile, ntiles, a.flags);
+  int u = blockIdx.x * units_per_block + slot;
+  if (leader) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+    if (u < nunits) issue(u);
+  }
+  sync_unit();
+  const RowAcc<T, U::WARP> acc{stage + 2 * RU * N + lrow * RS + comp * PADN, 0, 0xffffffffu};
+  const cx<T> *mine = stage + (comp * RU + lrow) * N + t;
+  const int ustride = gridDim.x * units_per_block;
+#pragma unroll 1
+  for (int it = 0; u < nunits; ++it, u += ustride) {
+    // the leader waits for the copy; the unit's barrier orders the other
+    // threads' reads after that wait and passes the outcome on
+    bool ok = true;
+    if (leader) ok = mbar_wait_bounded(bar, (uint32_t)(it & 1));
+    if constexpr (U::WARP) {
+      __syncwarp();
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    } else {
+      ok = __syncthreads_or(!ok) == 0;
+    }
+    if (!ok) {
+      // the copy for u may still land: give it one more bounded wait before leaving
+      if (leader) {
+        atomicOr(a.flags, kErrTimeout);
+        mbar_wait_bounded(bar, (uint32_t)(it & 1));
+      }
       return;
     }
-    const int inst = tile / groups, group = tile - inst * groups;
-    const int y = group * rows + pl.lrow;
-    cx<T> *b = buf(s);
     cx<T> v[1][E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[0][m] = b[(pl.comp * rows + pl.lrow) * N + pl.t + m * TT];
-    __syncthreads();  // the dense tile is read; its space now serves the exchanges
-    const RowAcc<T, row_warp_local(TT)> acc{b + pl.lrow * RS + pl.comp * PADN, 0, pl.mask};
-    const q4<T> *tab = tab_smem ? reinterpret_cast<const q4<T> *>(reinterpret_cast<unsigned char *>(b) +
-                                                                  (size_t)rows * RS * ES)
-                                : reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N;
-    double nsum[2] = {0.0, 0.0};
-    row_compute<T, LOGN, LOGE, F>(v, pl.t, pl.comp, pl.mask, pl.half, inst, y, acc, tab, a, nsum);
-    if constexpr (F & F_PART) row_partials(a, inst, group, groups, nsum);
-    cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + pl.comp) * a.ny + y) * N;
-#pragma unroll
-    for (int m = 0; m < E; ++m) p[pl.t + m * TT] = v[0][m];
-    __syncthreads();  // every thread is done with buffer s
-    if (threadIdx.x == 0) {
-      const int nt = tile + kPipe * gridDim.x;
-      if (nt < ntiles) {
-        fence_proxy_async();
-        issue(nt, s);
-      }
+    for (int m = 0; m < E; ++m) v[0][m] = mine[m * TT];
+    sync_unit();  // the staging buffer is read: refill it with the next rows
+    if (leader && u + ustride < nunits) {
+      fence_proxy_async();
+      issue(u + ustride);
     }
+    const int inst = u / upi, group = u - inst * upi;
+    const int y = group * RU + lrow;
+    double nsum[2] = {0.0, 0.0};
+    row_compute<T, LOGN, LOGE, F>(v, t, comp, 0xffffffffu, 16, inst, y, acc,
+                                  reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N, ac, nsum);
+    if constexpr (F & F_PART) {
+      if constexpr (U::WARP) warp_partials(a, inst, group, upi, nsum);
+      else row_partials(a, inst, group, upi, nsum);
+    }
+    cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N + t;
+#pragma unroll
+    for (int m = 0; m < E; ++m) p[m * TT] = v[0][m];
   }
 }
-
 
 // Columns per tile of the persistent column pass: a 128-byte row segment
 // where two tile buffers fit in about 110 KB and the block stays within 512

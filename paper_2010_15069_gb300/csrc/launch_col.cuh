@@ -7,11 +7,7 @@
 
 namespace spgpe {
 
-// Elements per thread of the column pass (one component per thread): 16
-// complex64 / 8 complex128 (16 from 2048 up, so that a column fits 512 threads).
-template <class T> constexpr int col_loge(int logn) {
-  return sizeof(T) == 4 ? std::min(logn, 4) : (logn >= 11 ? 4 : std::min(logn, 3));
-}
+template <class T> constexpr int col_loge(int logn) { return col_loge_for(logn, sizeof(cx<T>)); }
 
 template <class T> LaunchShape col_shape(int nx, int ny) {
   int logn = 0;
@@ -53,11 +49,9 @@ template <class T, int LOGN, bool IMAG> cudaError_t col_launch_n(ColArgs a, cuda
 template <class T, int LOGN> cudaError_t energy_launch_n(EnergyArgs a, cudaStream_t st, int *rb, int *cb) {
   // row part: the row-pass geometry
   {
-    constexpr int LOGE = std::min(LOGN, sizeof(T) == 4 ? 4 : 3);
+    constexpr int LOGE = erow_loge_for(LOGN, sizeof(cx<T>));
     auto kern = energy_row<T, LOGN, LOGE>;
-    int logn = 0;
-    while ((1 << logn) < a.nx) ++logn;
-    const int E = 1 << std::min(logn, sizeof(T) == 4 ? 4 : 3);
+    const int E = 1 << LOGE;
     const int TT = a.nx / E;
     const int rows = std::max(1, std::min(kRowMaxThreads / TT, a.ny));
     const size_t smem = (size_t)rows * row_stride(a.nx, sizeof(cx<T>)) * sizeof(cx<T>);

@@ -7,12 +7,7 @@
 
 namespace spgpe {
 
-// Elements per thread of the row pass (one component per thread): 16
-// complex64 or 8 complex128 values, 16 complex128 at nx = 4096 so that one
-// row fits a 512-thread block.
-template <class T> constexpr int row_loge(int logn) {
-  return sizeof(T) == 4 ? std::min(logn, 4) : (logn >= 12 ? 4 : std::min(logn, 3));
-}
+template <class T> constexpr int row_loge(int logn) { return row_loge_for(logn, sizeof(cx<T>)); }
 
 template <class T> LaunchShape row_shape(int nx, int ny) {
   int logn = 0;
@@ -84,42 +79,28 @@ template <class T> cudaError_t launch_row(int flags, RowArgs a, cudaStream_t st)
 
 // ---- persistent row pass
 
-// Rows per tile of the persistent pass: about 256 threads per block.
-template <class T> int rowp_rows(int nx, int ny) {
-  int logn = 0;
-  while ((1 << logn) < nx) ++logn;
-  const int TT = nx >> row_loge<T>(logn);
-  return std::max(1, std::min(kRowMaxThreads / (2 * TT), ny));
-}
-
 template <class T, int LOGN, int F> cudaError_t rowp_launch_n(RowArgs a, cudaStream_t st, int sms) {
   constexpr int LOGE = row_loge<T>(LOGN);
-  constexpr int N = 1 << LOGN, TT = N >> LOGE;
-  constexpr bool NEEDTAB = (F & (F_REND | F_RSTART)) != 0;
+  constexpr int N = 1 << LOGN, E = 1 << LOGE;
+  using U = RowUnit<N, E>;
+  if (a.ny < U::ROWS) return cudaErrorNotSupported;  // a unit would span instances: the plain pass
   auto kern = row_pass_p<T, LOGN, LOGE, F>;
-  const int rows = rowp_rows<T>(a.nx, a.ny);
-  const int threads = 2 * rows * TT;
-  const int es = sizeof(cx<T>);
-  // copy the x step table with each tile while two tile buffers stay under ~110 KB
-  bool tab = NEEDTAB && kPipe * rowp_buf_bytes(N, rows, es, true) <= 112 * 1024;
-  const size_t smem = kPipe * rowp_buf_bytes(N, rows, es, tab) + kPipe * sizeof(uint64_t);
-  if (smem > kMaxSmemPerBlock) return cudaErrorNotSupported;  // caller falls back to the plain pass
+  const int threads = rowu_block(N, E);
+  const int upb = U::WARP ? threads / 32 : 1;  // units per block
+  const size_t smem = rowu_smem(N, E, sizeof(cx<T>), Plan<LOGN, LOGE>::entries());
+  if (smem > kMaxSmemPerBlock) return cudaErrorNotSupported;
   static int granted = 0;
   cudaError_t e = grant_smem(kern, smem, granted);
   if (e != cudaSuccess) return e;
-  static int occ_threads = -1, occ_blocks = 0;
-  static size_t occ_smem = 0;
-  if (occ_threads != threads || occ_smem != smem) {
+  static int occ_blocks = -1;
+  if (occ_blocks < 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, threads, smem);
     if (e != cudaSuccess) return e;
-    occ_threads = threads;
-    occ_smem = smem;
   }
-  const int ntiles = a.ninst * (a.ny / rows);
-  const int grid = std::max(1, std::min(ntiles, std::max(1, occ_blocks) * sms));
-  a.rows = rows;
-  a.tab_in_smem = tab ? 1 : 0;
-  kern<<<grid, threads, smem, st>>>(a, ntiles);
+  const int nunits = a.ninst * (a.ny / U::ROWS);
+  const int grid = std::max(1, std::min((nunits + upb - 1) / upb, std::max(1, occ_blocks) * sms));
+  a.rows = U::ROWS;
+  kern<<<grid, threads, smem, st>>>(a, nunits);
   return cudaGetLastError();
 }
 

@@ -229,6 +229,29 @@ def test_split_runs_agree(dtype):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("dtype,nx,ny,ninst", [("c64", 8, 8, 2), ("c64", 64, 32, 3), ("c64", 256, 64, 2),
+                                               ("c64", 512, 16, 1), ("c64", 2048, 8, 1), ("c64", 4096, 8, 1),
+                                               ("c128", 128, 32, 2), ("c128", 512, 16, 1)])
+def test_persistent_and_plain_row_passes_agree(dtype, nx, ny, ninst, monkeypatch):
+    """The persistent row pass (per-unit prefetch) against the plain one-tile-per-
+    block pass: real time bit for bit (same arithmetic), imaginary time to the
+    rounding of the FP64 atom-number sums (their grouping differs)."""
+    p = coupled(nx, ny)
+    psi0 = np.stack([inputs.gaussian_spinor(p.grid, seed=20 + i) for i in range(ninst)])
+    out = {}
+    for mode in ("0", "2"):
+        monkeypatch.setenv("SPGPE_PERSISTENT", mode)
+        with ctx_for(p, dtype, ninst=ninst) as c:
+            a = to_dev(psi0, dtype)
+            c.step_real(a, 1e-3, 7)
+            b = a.clone()
+            c.step_imag(b, 1e-3, 9, sp.SPGPE_NORM_PER_COMPONENT)
+            out[mode] = (to_host(a), to_host(b))
+    assert np.array_equal(out["0"][0], out["2"][0])
+    tol = 1e-12 if dtype == "c128" else 2e-6
+    assert np.abs(out["0"][1] - out["2"][1]).max() < tol
+
+
 def test_cufft_comparator_matches_oracle(orc):
     p = coupled(64, 64)
     psi0 = inputs.gaussian_spinor(p.grid, seed=9)
