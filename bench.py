@@ -137,6 +137,77 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
+# ------------------------------------------------------- time to residual
+
+TTR_GRID, TTR_BOX, TTR_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK = 256, 12.0, 5e-3, 1e-8, 60000, 250
+
+
+def ttr_problems(B):
+    """B instances of the parameter sweep (g log-uniform in [50, 2000], g12/g in
+    [0.8, 1.2], Omega in [0, 6], detuning gradient in [0, 1], kL = 1, seed 3) on
+    256^2 over [-12, 12]^2, each from a vortex-seeded spinor (20 vortices)."""
+    n, L = TTR_GRID, TTR_BOX
+    prm = inputs.sweep_params(B, seed=3)
+    probs = [inputs.problem(n, n, L, L, Omega=q["Omega"], delta_slope=q["delta_slope"], g11=q["g"], g22=q["g"],
+                            g12=q["g12"], kL=1.0) for q in prm]
+    psi0 = np.stack([inputs.vortex_spinor(probs[0].grid, n_vortices=20, radius=5.0, seed=300 + i)
+                     for i in range(B)])
+    return probs, psi0
+
+
+def time_to_residual(B):
+    """Wall time until every instance has residual <= 1e-8, has stalled (no 1 %
+    gain in 40 checks: a metastable state) or has used its step budget: the
+    plain FP64 path (one complex128 context per instance, one after another)
+    against the batched complex64 -> complex128 ladder (one context for the
+    whole batch, finished instances frozen)."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    probs, psi0 = ttr_problems(B)
+    n, L = TTR_GRID, TTR_BOX
+
+    def ctx(ninst, idx):
+        c = sp.Context(n, n, L, L, "c128", ninst)
+        for k, i in enumerate(idx):
+            p = probs[i]
+            c.set_potentials_separable(k, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+        return c
+
+    plain_s, plain_res, plain_steps, plain = 0.0, [], [], []
+    for i in range(B):
+        with ctx(1, [i]) as c:
+            t = torch.from_numpy(psi0[i].copy()).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, st = c.relax(t, TTR_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK, give_up=True)
+            plain_s += time.perf_counter() - t0
+            plain_res.append(float(res[0]))
+            plain_steps.append(st[1])
+            plain.append(t.cpu().numpy())
+    with ctx(B, range(B)) as c:
+        t = torch.from_numpy(psi0.copy()).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, st = c.relax(t, TTR_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK, ladder=True, give_up=True)
+        ladder_s = time.perf_counter() - t0
+        e_lad = c.energy(t)[:, 0]
+        lad = t.cpu().numpy()
+    with ctx(B, range(B)) as c:
+        e_pl = c.energy(torch.from_numpy(np.stack(plain)).cuda())[:, 0]
+    both = [i for i in range(B) if plain_res[i] <= TTR_TOL and res[i] <= TTR_TOL]
+    return {"workload": f"{B} sweep instances, {n}x{n}, box [-{L:g},{L:g}]^2, kL=1, vortex-seeded, "
+                        f"dtau={TTR_DTAU:g}, check every {TTR_CHECK} steps, at most {TTR_MAX} steps per stage, "
+                        f"stalled instances given up after 40 checks",
+            "tol": TTR_TOL, "plain_fp64_unbatched_s": plain_s, "batched_ladder_s": ladder_s,
+            "speedup": plain_s / ladder_s,
+            "converged": {"plain": sum(r <= TTR_TOL for r in plain_res), "ladder": int((res <= TTR_TOL).sum()),
+                          "of": B},
+            "steps": {"plain_c128_per_instance": plain_steps, "ladder_c64": st[0], "ladder_c128": st[1]},
+            "agreement": {"max_rel_energy_diff": float(np.max(np.abs(e_lad[both] - e_pl[both]) / np.abs(e_pl[both])))
+                          if both else None,
+                          "max_abs_dpsi": float(np.abs(lad[both] - np.stack(plain)[both]).max()) if both else None}}
+
+
 # ------------------------------------------------------------- CPU oracle
 
 def oracle_rate(budget_s=12.0, max_steps=400):
@@ -332,6 +403,8 @@ def run_fused(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if world == 1 and args.ttr_instances > 0:
+        line["time_to_residual"] = time_to_residual(args.ttr_instances)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -345,6 +418,8 @@ def main():
     ap.add_argument("--impl", choices=["fused", "reference"], default="fused")
     ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES)
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--ttr-instances", type=int, default=8,
+                    help="sweep instances of the time-to-residual comparison (0: skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -125,23 +125,31 @@ int spgpe_step_imag(spgpe_ctx *ctx, void *psi, double dtau, int nsteps, int norm
  * number of steps).  Runs spgpe_step_imag in chunks of check_every steps, each
  * chunk ending with the discrete-map residual of its last step (defined as
  * for spgpe_step_imag), until every instance has residual <= tol or max_steps
- * steps have run.  dtau, norm_mode and target as for spgpe_step_imag.
- * flags = SPGPE_RELAX_LADDER on a complex128 context first relaxes a
- * complex64 copy of the spinor with the same model (the context's own
- * complex64 twin, allocated on first use): rounded once, stepped in complex64
- * until every residual is <= max(tol, handoff), or, with handoff = 0, until
- * the residual has reached complex64's rounding floor (about 2^-24 / dtau
- * times a modest factor) and stops improving; then widened back into psi and
- * relaxed in complex128 to tol.  The rounding of every complex64 step also
- * excites slowly relaxing modes that a smooth initial state leaves untouched,
- * so the ladder pays off for initial states far from the ground state (random
- * or vortex-seeded), and a hand-off residual well above the floor limits that
- * noise.  The flag is ignored on complex64 contexts; handoff >= 0.
- * residual_out (host, nullable): ninst doubles, the last residual of each
- * instance.  steps_out (host, nullable): {steps run in complex64 by the
- * ladder, steps run in the context's precision}.  Returns SPGPE_OK also when
+ * steps have run.  An instance within tol is frozen (no longer stepped) while
+ * the others go on.  dtau, norm_mode and target as for spgpe_step_imag.
+ *
+ * flags, a bitwise or of:
+ *  SPGPE_RELAX_LADDER (complex128 contexts; ignored on complex64): relax a
+ *   complex64 copy of the spinor with the same model first (the context's
+ *   own complex64 twin, allocated on first use): rounded once, stepped in
+ *   complex64 until every residual is <= max(tol, handoff), or, with
+ *   handoff = 0, until each instance's residual has reached complex64's
+ *   rounding floor (below 2^-18 / dtau) and improves by less than a fifth per
+ *   chunk; then widened back into psi and relaxed in complex128 to tol.  Each
+ *   stage may run max_steps steps.  The rounding of every complex64 step
+ *   also excites slowly relaxing modes that a smooth initial state leaves
+ *   untouched, so the ladder pays off for initial states far from the ground
+ *   state (random or vortex-seeded), and a hand-off residual well above the
+ *   floor limits that noise.
+ *  SPGPE_RELAX_GIVE_UP: also freeze an instance whose smallest residual so
+ *   far has not dropped by 1 % in 40 chunks (a metastable state); its
+ *   residual stays above tol.
+ * handoff >= 0.  residual_out (host, nullable): ninst doubles, the last
+ * residual of each instance.  steps_out (host, nullable): {steps run in
+ * complex64 by the ladder, steps run in the context's precision}, counted
+ * until the last instance of the stage was done.  Returns SPGPE_OK also when
  * max_steps ran out first (compare residual_out with tol).  Synchronises. */
-enum { SPGPE_RELAX_LADDER = 1 };
+enum { SPGPE_RELAX_LADDER = 1, SPGPE_RELAX_GIVE_UP = 2 };
 int spgpe_relax(spgpe_ctx *ctx, void *psi, double dtau, double tol, int max_steps, int check_every,
                 int norm_mode, const double *target, int flags, double handoff, double *residual_out,
                 int *steps_out);

@@ -20,11 +20,12 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SPGPE_RELAX_LADDER,
-                   SpgpeError, check, load)
+from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SPGPE_RELAX_GIVE_UP,
+                   SPGPE_RELAX_LADDER, SpgpeError, check, load)
 
 __all__ = [
-    "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SpgpeError",
+    "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SPGPE_RELAX_GIVE_UP",
+    "SpgpeError",
     "Context", "load",
     "spgpe_init_grid", "spgpe_init_batch", "spgpe_set_potentials", "spgpe_set_potentials_separable",
     "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_energy", "spgpe_norm", "spgpe_sync",
@@ -229,9 +230,10 @@ class Context:
                                residual, self.ninst)
 
     def relax(self, psi, dtau, tol, max_steps, check_every=200, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5),
-              ladder=False, handoff=0.0):
+              ladder=False, handoff=0.0, give_up=False):
+        flags = (SPGPE_RELAX_LADDER if ladder else 0) | (SPGPE_RELAX_GIVE_UP if give_up else 0)
         return spgpe_relax(self._ctx, self._check_psi(psi), dtau, tol, max_steps, check_every, norm_mode, target,
-                           SPGPE_RELAX_LADDER if ladder else 0, handoff, self.ninst)
+                           flags, handoff, self.ninst)
 
     def cufft_step_real(self, psi, dt, nsteps):
         spgpe_cufft_step_real(self._ctx, self._check_psi(psi), dt, nsteps)

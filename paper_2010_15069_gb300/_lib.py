@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspgpe.so")
 
 SPGPE_C64, SPGPE_C128 = 1, 2
 SPGPE_NORM_TOTAL, SPGPE_NORM_PER_COMPONENT = 0, 1
-SPGPE_RELAX_LADDER = 1
+SPGPE_RELAX_LADDER, SPGPE_RELAX_GIVE_UP = 1, 2
 STATUS = {0: "SPGPE_OK", -1: "SPGPE_EINVAL", -2: "SPGPE_ENOMEM", -3: "SPGPE_ECUDA",
           -4: "SPGPE_ENONFINITE", -5: "SPGPE_ETIMEOUT", -6: "SPGPE_ESTATE"}
 

@@ -25,6 +25,8 @@ thread_local std::string g_init_error;
 
 bool pow2_in_range(int n) { return n >= 8 && n <= 4096 && (n & (n - 1)) == 0; }
 
+constexpr int kResidualBlocks = 128;  // blocks per instance of the residual reduction
+
 }  // namespace
 
 struct spgpe_ctx {
@@ -52,6 +54,8 @@ struct spgpe_ctx {
   unsigned *d_counters = nullptr;
   double *d_scale = nullptr;
   int *d_flags = nullptr;
+  int *d_active = nullptr;    // [ninst] per-instance step mask (relaxation freezes converged instances)
+  bool use_active = false;
   void *d_scratch = nullptr;  // psi-sized: energy transform / residual previous state
   void *d_stage = nullptr;    // psi-sized: staging of host spinors
   double tab_dt = NAN;
@@ -147,7 +151,7 @@ void free_all(spgpe_ctx *c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   void *ps[] = {c->d_twx, c->d_twy, c->d_twe, c->d_tabx, c->d_taby, c->d_rawx, c->d_rawy, c->d_pot2d, c->d_kxt,
-                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_flags, c->d_scratch,
+                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_flags, c->d_active, c->d_scratch,
                 c->d_stage};
   for (void *p : ps)
     if (p) cudaFree(p);
@@ -364,6 +368,7 @@ RowArgs row_args(spgpe_ctx *c, void *psi, double dt) {
   a.tgt1 = 0.5;
   a.norm_mode = 0;
   a.wgt = c->dx * c->dy;
+  a.active = c->use_active ? c->d_active : nullptr;
   a.flags = c->d_flags;
   a.nx = c->nx;
   a.ny = c->ny;
@@ -380,6 +385,7 @@ ColArgs col_args(spgpe_ctx *c, void *psi) {
   a.inv_d = 1.0 / ((double)c->nx * c->ny);
   a.inv_f = (float)a.inv_d;
   a.flags = c->d_flags;
+  a.active = c->use_active ? c->d_active : nullptr;
   a.nx = c->nx;
   a.ny = c->ny;
   a.ninst = c->ninst;
@@ -557,7 +563,8 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
       (r = dev_alloc(c, (void **)&c->d_partials, c->n_partials * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_counters, (size_t)ninst * sizeof(unsigned))) ||
       (r = dev_alloc(c, (void **)&c->d_scale, (size_t)ninst * 2 * sizeof(double))) ||
-      (r = dev_alloc(c, (void **)&c->d_flags, sizeof(int)))) {
+      (r = dev_alloc(c, (void **)&c->d_flags, sizeof(int))) ||
+      (r = dev_alloc(c, (void **)&c->d_active, (size_t)ninst * sizeof(int)))) {
     g_init_error = c->err;
     free_all(c);
     delete c;
@@ -604,6 +611,59 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
     return r;
   }
   *out = c;
+  return SPGPE_OK;
+}
+
+// nsteps imaginary-time steps of a device spinor, all on the context's stream
+// and without synchronising.  With `residual`, the last step also leaves the
+// residual partials (||Psi_{n+1} - Psi_n||^2, ||Psi_n||^2 per block and
+// instance) in d_partials for imag_collect.
+int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, double t0, double t1,
+                 bool residual) {
+  int r;
+  if ((r = ensure_tables(c, dtau, 1))) return r;
+  if (residual && (r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
+  RowArgs ra = row_args(c, p, dtau);
+  ra.tgt0 = t0;
+  ra.tgt1 = t1;
+  ra.norm_mode = norm_mode;
+  const ColArgs ca = col_args(c, p);
+  for (int s = 1; s <= nsteps; ++s) {
+    if (s == nsteps && residual) {
+      // Keep Psi_n (normalised) for the residual of the last step.
+      if (s > 1) CK(c, row(c, kImagScale, ra));
+      CK(c, cudaMemcpyAsync(c->d_scratch, p, c->psi_bytes(), cudaMemcpyDeviceToDevice, c->st));
+      CK(c, row(c, kImagFirst, ra));
+    } else {
+      CK(c, row(c, s == 1 ? kImagFirst : kImagB, ra));
+    }
+    CK(c, col(c, true, ca));
+    CK(c, row(c, kImagA, ra));
+  }
+  CK(c, row(c, kImagScale, ra));
+  if (residual) {
+    ++c->last_launches;
+    if (c->dtype == SPGPE_C64)
+      CK(c, launch_residual<float>(p, c->d_scratch, c->plane(), c->ninst, c->d_partials, kResidualBlocks, c->st));
+    else
+      CK(c, launch_residual<double>(p, c->d_scratch, c->plane(), c->ninst, c->d_partials, kResidualBlocks, c->st));
+  }
+  return SPGPE_OK;
+}
+
+// Wait for the residual partials of imag_enqueue and reduce them on the host.
+int imag_collect(spgpe_ctx *c, double dtau, double *residual_out) {
+  std::vector<double> h((size_t)c->ninst * kResidualBlocks * 2);
+  CK(c, cudaMemcpyAsync(h.data(), c->d_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  for (int i = 0; i < c->ninst; ++i) {
+    double num = 0, den = 0;
+    for (int b = 0; b < kResidualBlocks; ++b) {
+      num += h[((size_t)i * kResidualBlocks + b) * 2];
+      den += h[((size_t)i * kResidualBlocks + b) * 2 + 1];
+    }
+    residual_out[i] = std::sqrt(num / den) / dtau;
+  }
   return SPGPE_OK;
 }
 
@@ -746,48 +806,11 @@ int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_m
       for (int i = 0; i < c->ninst; ++i) residual_out[i] = NAN;
     return SPGPE_OK;
   }
-  if ((r = ensure_tables(c, dtau, 1))) return r;
-  if (residual_out && (r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
   void *p;
   bool host;
   if ((r = begin_psi(c, psi, &p, &host))) return r;
-  RowArgs ra = row_args(c, p, dtau);
-  ra.tgt0 = t0;
-  ra.tgt1 = t1;
-  ra.norm_mode = norm_mode;
-  const ColArgs ca = col_args(c, p);
-  for (int s = 1; s <= nsteps; ++s) {
-    if (s == nsteps && residual_out) {
-      // Keep Psi_n (normalised) for the residual of the last step.
-      if (s > 1) CK(c, row(c, kImagScale, ra));
-      CK(c, cudaMemcpyAsync(c->d_scratch, p, c->psi_bytes(), cudaMemcpyDeviceToDevice, c->st));
-      CK(c, row(c, kImagFirst, ra));
-    } else {
-      CK(c, row(c, s == 1 ? kImagFirst : kImagB, ra));
-    }
-    CK(c, col(c, true, ca));
-    CK(c, row(c, kImagA, ra));
-  }
-  CK(c, row(c, kImagScale, ra));
-  if (residual_out) {
-    const int blocks = 128;
-    ++c->last_launches;
-    if (c->dtype == SPGPE_C64)
-      CK(c, launch_residual<float>(p, c->d_scratch, c->plane(), c->ninst, c->d_partials, blocks, c->st));
-    else
-      CK(c, launch_residual<double>(p, c->d_scratch, c->plane(), c->ninst, c->d_partials, blocks, c->st));
-    std::vector<double> h((size_t)c->ninst * blocks * 2);
-    CK(c, cudaMemcpyAsync(h.data(), c->d_partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    CK(c, cudaStreamSynchronize(c->st));
-    for (int i = 0; i < c->ninst; ++i) {
-      double num = 0, den = 0;
-      for (int b = 0; b < blocks; ++b) {
-        num += h[((size_t)i * blocks + b) * 2];
-        den += h[((size_t)i * blocks + b) * 2 + 1];
-      }
-      residual_out[i] = std::sqrt(num / den) / dtau;
-    }
-  }
+  if ((r = imag_enqueue(c, p, dtau, nsteps, norm_mode, t0, t1, residual_out != nullptr))) return r;
+  if (residual_out && (r = imag_collect(c, dtau, residual_out))) return r;
   if ((r = end_psi(c, psi, host))) return r;
   if (residual_out || host) return read_flags(c);
   return SPGPE_OK;
@@ -980,28 +1003,61 @@ int ensure_twin(spgpe_ctx *c) {
 
 // Imaginary-time steps in chunks of `check`, each ending with the residual of
 // its last step, until every instance is within tol or max_steps have run.
-// to_floor: also stop once the largest residual has reached the rounding
-// floor of complex64 (below 2^-18 / dtau) and improves by less than a fifth
-// from one chunk to the next.
+// An instance that is done is frozen (the passes skip it) while the others
+// go on; its residual stays the last one measured.  to_floor: an instance is
+// also done once its residual has reached the rounding floor of complex64
+// (below 2^-18 / dtau) and improves by less than a fifth from one chunk to
+// the next.  give_up: an instance is also done once its smallest residual so
+// far has not dropped by 1 % in kStallChecks chunks (a metastable state).
+constexpr int kStallChecks = 40;
 int relax_stage(spgpe_ctx *c, void *p, double dtau, double tol, int max_steps, int check, int norm_mode,
-                const double *target, bool to_floor, std::vector<double> &res, int *steps, int *launches) {
+                const double *target, bool to_floor, bool give_up, std::vector<double> &res, int *steps,
+                int *launches) {
   const double floor64 = std::ldexp(1.0, -18) / dtau;
-  double prev = INFINITY;
-  int done = 0;
-  while (done < max_steps) {
+  const int ni = c->ninst;
+  std::vector<int> act((size_t)ni, 1), since((size_t)ni, 0);
+  std::vector<double> prev((size_t)ni, INFINITY), best((size_t)ni, INFINITY), r((size_t)ni);
+  int done = 0, nact = ni;
+  CK(c, cudaMemcpyAsync(c->d_active, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  c->use_active = true;
+  auto finish = [&](int code) {
+    c->use_active = false;
+    *steps = done;
+    return code;
+  };
+  while (done < max_steps && nact > 0) {
     const int n = std::min(check, max_steps - done);
-    const int r = spgpe_step_imag(c, p, dtau, n, norm_mode, target, res.data());
-    if (r) return r;
+    const int rc = spgpe_step_imag(c, p, dtau, n, norm_mode, target, r.data());
+    if (rc) return finish(rc);
     *launches += c->last_launches;
     done += n;
-    double rmax = 0.0;
-    for (double v : res) rmax = std::isnan(v) ? INFINITY : std::max(rmax, v);
-    if (rmax <= tol) break;
-    if (to_floor && rmax < floor64 && rmax > 0.8 * prev) break;
-    prev = rmax;
+    bool changed = false;
+    for (int i = 0; i < ni; ++i) {
+      if (!act[(size_t)i]) continue;
+      const double v = std::isnan(r[(size_t)i]) ? INFINITY : r[(size_t)i];
+      res[(size_t)i] = v;
+      if (v < 0.99 * best[(size_t)i]) {
+        best[(size_t)i] = v;
+        since[(size_t)i] = 0;
+      } else {
+        ++since[(size_t)i];
+      }
+      if (v <= tol || (to_floor && v < floor64 && v > 0.8 * prev[(size_t)i]) ||
+          (give_up && since[(size_t)i] >= kStallChecks)) {
+        act[(size_t)i] = 0;
+        --nact;
+        changed = true;
+      }
+      prev[(size_t)i] = v;
+    }
+    if (changed && nact > 0) {
+      // a pageable-memory copy: the host array is consumed before the call returns
+      const cudaError_t e = cudaMemcpyAsync(c->d_active, act.data(), act.size() * sizeof(int),
+                                            cudaMemcpyHostToDevice, c->st);
+      if (e != cudaSuccess) return finish(cuda_fail(c, e, "active mask upload"));
+    }
   }
-  *steps = done;
-  return SPGPE_OK;
+  return finish(SPGPE_OK);
 }
 
 }  // namespace
@@ -1015,8 +1071,9 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
   if (!psi || !(dtau > 0) || !std::isfinite(dtau) || !(tol > 0) || max_steps < 1 || check_every < 1 ||
       !(handoff >= 0) || !std::isfinite(handoff))
     return fail(c, SPGPE_EINVAL, "bad psi, dtau, tol, max_steps, check_every or handoff");
-  if (flags & ~SPGPE_RELAX_LADDER) return fail(c, SPGPE_EINVAL, "unknown flags");
+  if (flags & ~(SPGPE_RELAX_LADDER | SPGPE_RELAX_GIVE_UP)) return fail(c, SPGPE_EINVAL, "unknown flags");
   const bool ladder = (flags & SPGPE_RELAX_LADDER) && c->dtype == SPGPE_C128;
+  const bool give_up = (flags & SPGPE_RELAX_GIVE_UP) != 0;
   void *p;
   bool host;
   if ((r = begin_psi(c, psi, &p, &host))) return r;
@@ -1028,16 +1085,14 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
     CK(c, launch_convert(p, 16, c->d_psi64, 8, n, c->sms, c->st));
     // complex64 down to the hand-off residual, or (handoff = 0) its rounding floor
     r = relax_stage(c->twin, c->d_psi64, dtau, std::max(tol, handoff), max_steps, check_every, norm_mode, target,
-                    handoff == 0.0, res, &s64, &launches);
+                    handoff == 0.0, give_up, res, &s64, &launches);
     if (r) return fail(c, r, "complex64 stage: " + c->twin->err);
     CK(c, launch_convert(c->d_psi64, 8, p, 16, n, c->sms, c->st));
     launches += 2;
   }
-  if (max_steps - s64 >= 1) {
-    // a context's own steps; the staged host spinor is already on the device
-    r = relax_stage(c, p, dtau, tol, max_steps - s64, check_every, norm_mode, target, false, res, &s, &launches);
-    if (r) return r;
-  }
+  // the context's own steps (the staged host spinor is already on the device)
+  r = relax_stage(c, p, dtau, tol, max_steps, check_every, norm_mode, target, false, give_up, res, &s, &launches);
+  if (r) return r;
   c->last_launches = launches;
   if ((r = end_psi(c, psi, host))) return r;
   if (residual_out)

@@ -47,6 +47,7 @@ struct RowArgs {
   double tgt0, tgt1;      // target atom numbers
   int norm_mode;          // 0 total, 1 per component
   double wgt;             // dx * dy
+  const int *active;      // [ninst] nonzero: step this instance (null: all); frozen instances are skipped
   int *flags;             // bit 0: non-finite or zero norm met
   int nx, ny, ninst, rows;
 };
@@ -57,6 +58,7 @@ struct ColArgs {
   double inv_d;           // 1/(nx ny), an exact power of two
   float inv_f;
   int *flags;             // error bits (persistent pass: bit 1 = transfer wait timed out)
+  const int *active;      // [ninst] as in RowArgs
   const void *kxt;        // [ninst][2][nx] complex a_j(kx) - 1
   const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
   const void *tw;         // twiddle table of the y plan (see TwType in fft_core.cuh)

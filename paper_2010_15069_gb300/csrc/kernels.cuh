@@ -499,6 +499,7 @@ row_pass(const RowArgs a) {
   cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
   const RowPlace pl = row_place<TT>();
   const int inst = blockIdx.y;
+  if (a.active && !a.active[inst]) return;  // frozen instance (uniform over the block)
   const int y = blockIdx.x * a.rows + pl.lrow;
   cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + pl.comp) * a.ny + y) * N;
   constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
@@ -551,6 +552,7 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
   const int C = a.C;
   const int c = threadIdx.x % C, t = threadIdx.x / C;
   const int comp = blockIdx.y, inst = blockIdx.z;
+  if (a.active && !a.active[inst]) return;  // frozen instance (uniform over the block)
   const int kx = blockIdx.x * C + c;
   cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + ((long)inst * 2 + comp) * (long)N * a.nx + kx;
   const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};

@@ -24,17 +24,6 @@ __host__ __device__ constexpr size_t colp_buf_bytes(int n, int c, int es) {
   return ((size_t)col_smem_elems(n, c, es) * es + 127) / 128 * 128;
 }
 
-// A wait for tile i ran out: record the error, then give the other copy this
-// block still has in flight (tile + gridDim.x, if it was issued) its own
-// bounded wait, so the block does not exit with a transfer landing in its
-// shared memory.
-__device__ __forceinline__ void drain_after_timeout(uint64_t *bar, int i, int tile, int ntiles, int *flags) {
-  if (threadIdx.x == 0) {
-    atomicOr(flags, kErrTimeout);
-    if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[(i + 1) % kPipe], (uint32_t)(((i + 1) / kPipe) & 1));
-  }
-}
-
 // ------------------------------------------------ persistent row pass
 //
 // The rows are handed out in units: a warp's worth of rows when a row lies
@@ -183,7 +172,14 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
   RowArgs ac = a;
   ac.tw = tw;
 
-  int u = blockIdx.x * units_per_block + slot;
+  const int ustride = gridDim.x * units_per_block;
+  // the first unit at or after v (in steps of ustride) whose instance is not frozen
+  auto next_active = [&](int v) {
+    if (a.active)
+      while (v < nunits && !a.active[v / upi]) v += ustride;
+    return v;
+  };
+  int u = next_active(blockIdx.x * units_per_block + slot);
   if (leader) {
     mbar_init(bar, 1);
     mbar_fence_init();
@@ -192,9 +188,8 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
   sync_unit();
   const RowAcc<T, U::WARP> acc{stage + 2 * RU * N + lrow * RS + comp * PADN, 0, 0xffffffffu};
   const cx<T> *mine = stage + (comp * RU + lrow) * N + t;
-  const int ustride = gridDim.x * units_per_block;
 #pragma unroll 1
-  for (int it = 0; u < nunits; ++it, u += ustride) {
+  for (int it = 0; u < nunits; ++it) {
     // the leader waits for the copy; the unit's barrier orders the other
     // threads' reads after that wait and passes the outcome on
     bool ok = true;
@@ -217,9 +212,10 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
 #pragma unroll
     for (int m = 0; m < E; ++m) v[0][m] = mine[m * TT];
     sync_unit();  // the staging buffer is read: refill it with the next rows
-    if (leader && u + ustride < nunits) {
+    const int un = next_active(u + ustride);
+    if (leader && un < nunits) {
       fence_proxy_async();
-      issue(u + ustride);
+      issue(un);
     }
     const int inst = u / upi, group = u - inst * upi;
     const int y = group * RU + lrow;
@@ -233,6 +229,7 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
     cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N + t;
 #pragma unroll
     for (int m = 0; m < E; ++m) p[m * TT] = v[0][m];
+    u = un;
   }
 }
 
@@ -269,23 +266,38 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     for (int h = 0; h < N; h += BOXH) tma_g2s_2d(buf(s) + h * C, &map, cg * C * XMUL, pc * N + h, &bar[s]);
   };
 
+  // the first tile at or after v (in steps of gridDim.x) whose instance is not frozen
+  auto next_active = [&](int v) {
+    if (a.active)
+      while (v < ntiles && !a.active[v / (2 * cgroups)]) v += gridDim.x;
+    return v;
+  };
+  // the tile being processed (buffer i % 2) and the one streaming into the
+  // other buffer (ntiles: none)
+  static_assert(kPipe == 2, "two tile buffers");
+  int tile = next_active(blockIdx.x);
+  int nxt = tile < ntiles ? next_active(tile + gridDim.x) : ntiles;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kPipe; ++s) mbar_init(&bar[s], 1);
+    for (int q = 0; q < kPipe; ++q) mbar_init(&bar[q], 1);
     mbar_fence_init();
-    for (int s = 0; s < kPipe; ++s)
-      if (blockIdx.x + s * gridDim.x < ntiles) issue(blockIdx.x + s * gridDim.x, s);
+    if (tile < ntiles) issue(tile, 0);
+    if (nxt < ntiles) issue(nxt, 1);
   }
   for (int k = threadIdx.x; k < N; k += blockDim.x) btab[k] = reinterpret_cast<const cx<T> *>(a.kyt)[k];
   __syncthreads();
   T inv;
   if constexpr (sizeof(T) == 4) inv = a.inv_f; else inv = a.inv_d;
 
-  int i = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
-    const int s = i % kPipe;
-    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i / kPipe) & 1));
+  for (int i = 0; tile < ntiles; ++i) {
+    const int s = i & 1;
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i >> 1) & 1));
     if (!__syncthreads_and(ok)) {
-      drain_after_timeout(bar, i, tile, ntiles, a.flags);
+      // a wait ran out: record it, and give the copy still in flight into the
+      // other buffer (if any) its own bounded wait before leaving
+      if (threadIdx.x == 0) {
+        atomicOr(a.flags, kErrTimeout);
+        if (nxt < ntiles) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+      }
       return;
     }
     const int pc = tile / cgroups, kx = (tile - pc * cgroups) * C + c;
@@ -302,13 +314,14 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
 #pragma unroll
     for (int m = 0; m < E; ++m) col[t * a.nx + m * rs] = v[0][m];
     __syncthreads();  // every thread is done with buffer s
-    if (threadIdx.x == 0) {
-      const int nt = tile + kPipe * gridDim.x;
-      if (nt < ntiles) {
-        fence_proxy_async();
-        issue(nt, s);
-      }
+    // refill buffer s with the tile after the one waiting in the other buffer
+    const int after = nxt < ntiles ? next_active(nxt + gridDim.x) : ntiles;
+    if (threadIdx.x == 0 && after < ntiles) {
+      fence_proxy_async();
+      issue(after, s);
     }
+    tile = nxt;
+    nxt = after;
   }
 }
 

@@ -84,3 +84,29 @@ def test_relax_rejects_bad_arguments():
             args.update(kw)
             with pytest.raises(sp.SpgpeError, match="EINVAL"):
                 c.relax(t, **args)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batched_relaxation_freezes_each_instance_where_it_converged_alone(dtype):
+    """Instances converge after different numbers of chunks; a converged one
+    is frozen while the rest go on, so every instance of the batch ends with
+    the bits of its own single-instance relaxation."""
+    p = small_problem()
+    npt = np.complex64 if dtype == "c64" else np.complex128
+    tol = 1e-8 if dtype == "c128" else 1e-4
+    psi0 = np.stack([inputs.vortex_spinor(p.grid, n_vortices=2 + 3 * i, radius=3.0, seed=50 + i)
+                     for i in range(3)]).astype(npt)
+    with ctx(p, dtype, ninst=3) as c:
+        t = torch.from_numpy(psi0.copy()).cuda()
+        res, (_, steps) = c.relax(t, DTAU, tol, 40000, check_every=100)
+        got = t.cpu().numpy()
+    alone = []
+    for i in range(3):
+        with ctx(p, dtype) as c1:
+            t1 = torch.from_numpy(psi0[i].copy()).cuda()
+            r1, (_, s1) = c1.relax(t1, DTAU, tol, 40000, check_every=100)
+            alone.append((t1.cpu().numpy(), r1[0], s1))
+    assert steps == max(a[2] for a in alone)
+    for i in range(3):
+        assert res[i] == alone[i][1]
+        assert np.array_equal(got[i], alone[i][0]), i
