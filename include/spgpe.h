@@ -74,6 +74,21 @@ int spgpe_init_grid(spgpe_ctx **out, int nx, int ny, double xmax, double ymax,
 int spgpe_init_batch(spgpe_ctx **out, int nx, int ny, double xmax, double ymax,
                      int ninst, int dtype, void *cuda_stream);
 
+/* A batch over several grid sizes (parameter sweeps over grids, e.g. 64
+ * instances at 256^2 with 16 at 512^2 and 4 at 1024^2).  Size class k holds
+ * ninst[k] instances of an nx[k] x ny[k] grid over [-xmax[k], xmax[k]) x
+ * [-ymax[k], ymax[k]); instances are numbered class by class, and the spinor
+ * buffer holds them back to back in that order, each [2][ny][nx].  Each
+ * class runs on a CUDA stream of its own, started after the work already on
+ * cuda_stream and joined back into it, so the classes of one call run side
+ * by side, their persistent passes sharing the SMs in proportion to their
+ * points.  Every call below accepts such a context: instance indices and
+ * per-instance outputs are global; spgpe_set_potentials (2D arrays) and
+ * spgpe_set_potentials_separable with inst = -1 need all classes of one
+ * size.  nclass in [1, 64], at most 65535 instances in all. */
+int spgpe_init_multi(spgpe_ctx **out, int nclass, const int *nx, const int *ny, const int *ninst,
+                     const double *xmax, const double *ymax, int dtype, void *cuda_stream);
+
 /* Potentials and couplings of Eqs. 3-8 for every instance.  V, delta, Omega
  * are host FP64 arrays [ny][nx] (row-major), NULL meaning zero; they are
  * copied (the caller may free them on return) and stored in the working
@@ -142,8 +157,8 @@ int spgpe_step_imag(spgpe_ctx *ctx, void *psi, double dtau, int nsteps, int norm
  *   state (random or vortex-seeded), and a hand-off residual well above the
  *   floor limits that noise.
  *  SPGPE_RELAX_GIVE_UP: also freeze an instance whose smallest residual so
- *   far has not dropped by 1 % in 40 chunks (a metastable state); its
- *   residual stays above tol.
+ *   far has not halved in 40 chunks (a metastable state, or a relaxation far
+ *   too slow for the budget); its residual stays above tol.
  * handoff >= 0.  residual_out (host, nullable): ninst doubles, the last
  * residual of each instance.  steps_out (host, nullable): {steps run in
  * complex64 by the ladder, steps run in the context's precision}, counted
@@ -153,6 +168,18 @@ enum { SPGPE_RELAX_LADDER = 1, SPGPE_RELAX_GIVE_UP = 2 };
 int spgpe_relax(spgpe_ctx *ctx, void *psi, double dtau, double tol, int max_steps, int check_every,
                 int norm_mode, const double *target, int flags, double handoff, double *residual_out,
                 int *steps_out);
+
+/* Autotuning of the pass schedule: for the grid of a single-size context, or
+ * for every size class of a multi-size batch, time real-time steps S(dt) of
+ * each of the four variants (bit 0 of the variant: persistent row pass, in
+ * which each warp or block streams its next rows into shared memory while it
+ * transforms the current ones, else one row group per block; bit 1:
+ * persistent TMA column pass, else one column tile per block) on a scratch
+ * copy of psi (psi itself is not changed), and keep the fastest for all later
+ * calls (complex64 twins included).  choice_out (host, nullable): the chosen
+ * variant per class (one entry for a single-size context); ms_out (host,
+ * nullable): its time per step in milliseconds.  Synchronises. */
+int spgpe_autotune(spgpe_ctx *ctx, const void *psi, double dt, int *choice_out, double *ms_out);
 
 /* Energy functional whose variation is H Psi, per instance:
  * out[6*i .. 6*i+5] = {E_total, E_kinetic (incl. -kL kx sigma_z), E_trap,
@@ -164,6 +191,34 @@ int spgpe_energy(spgpe_ctx *ctx, const void *psi, double *out);
 /* Atom numbers per instance, out[2*i] = N_up, out[2*i+1] = N_dn, FP64
  * accumulation; synchronises.  ENONFINITE if a sum is not finite. */
 int spgpe_norm(spgpe_ctx *ctx, const void *psi, double *out);
+
+/* Observables of the spin-Hall ground states (Sec. 6), per instance:
+ * out[4*i .. 4*i+3] = {s, n_up, n_dn, R99}.
+ *  s: phase-separation parameter (Eq. 14), read as
+ *     1 - sum rho_up rho_dn / sqrt(sum rho_up^2 sum rho_dn^2) over the grid
+ *     (0 for proportional densities, 1 for disjoint ones).
+ *  R99: radius of the circle about the trap centre (0, 0) that encloses 99 %
+ *     of the total atom number (radii binned in widths min(dx, dy)/2; the
+ *     upper edge of the first bin at which the cumulative number reaches 99 %).
+ *  n_j: winding number of arg psi_j around that circle, counter-clockwise,
+ *     from 4 max(nx, ny) equally spaced points with psi_j bilinearly
+ *     interpolated on the periodic grid (phase steps wrapped into (-pi, pi],
+ *     summed in FP64, divided by 2 pi and rounded); the circulation of
+ *     Eq. 15 is 2 pi n_j (hbar = m = 1).
+ * Synchronises.  ENONFINITE if a value is not finite (e.g. a zero spinor). */
+int spgpe_observables(spgpe_ctx *ctx, const void *psi, double *out);
+
+/* Annealing noise of the ground-state protocol (Sec. 6: the first
+ * imaginary-time segment is perturbed now and then with Gaussian noise):
+ * psi += sigma xi, xi complex standard normal (E|xi|^2 = 1), independent per
+ * element.  Element e (component-major, then row-major) of global instance i
+ * takes draws 2E and 2E + 1, E = i * 2 nx ny + e, of the counter-based
+ * SplitMix64 stream `seed` (draw c = output function of seed + (c + 1)
+ * 0x9E3779B97F4A7C15; Steele, Lea & Flood 2014), as uniforms u = (draw >> 11)
+ * 2^-53, and xi = sqrt(-ln(1 - u1)) e^{2 pi i u2}.  The spinor is not
+ * renormalised (the next imaginary-time step does that).  Stream-ordered;
+ * a host spinor makes the call synchronous.  EINVAL for sigma < 0 or NaN. */
+int spgpe_add_noise(spgpe_ctx *ctx, void *psi, double sigma, unsigned long long seed);
 
 /* Wait for the context's stream and report an error recorded on the device
  * by an earlier asynchronous step (ENONFINITE), clearing it. */

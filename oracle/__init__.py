@@ -67,8 +67,14 @@ def _load():
                                      ctypes.c_int, ctypes.c_int, P, P]
             lib.orc_norm.argtypes = [ctypes.POINTER(_Model), P, P]
             lib.orc_energy.argtypes = [ctypes.POINTER(_Model), P, P]
-            for f in (lib.orc_fft2, lib.orc_apply, lib.orc_step, lib.orc_norm, lib.orc_energy):
+            lib.orc_observables.argtypes = [ctypes.POINTER(_Model), P, ctypes.c_int, P]
+            lib.orc_add_noise.argtypes = [ctypes.POINTER(_Model), P, ctypes.c_double, ctypes.c_ulonglong,
+                                          ctypes.c_long]
+            for f in (lib.orc_fft2, lib.orc_apply, lib.orc_step, lib.orc_norm, lib.orc_energy,
+                      lib.orc_observables, lib.orc_add_noise):
                 f.restype = None
+            lib.orc_splitmix64.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong]
+            lib.orc_splitmix64.restype = ctypes.c_ulonglong
             _lib = lib
     return _lib
 
@@ -137,6 +143,26 @@ class Model:
         out = np.zeros(6)
         _load().orc_energy(ctypes.byref(self._c), _ptr(psi), _ptr(out))
         return out
+
+
+    def observables(self, psi, npts=None):
+        """{s (Eq. 14), n_up, n_dn (Eq. 15 windings), R99} as a length-4 array; the
+        contour has 4 max(nx, ny) points unless npts is given."""
+        psi = self._psi(psi)
+        out = np.zeros(4)
+        _load().orc_observables(ctypes.byref(self._c), _ptr(psi), int(npts or 4 * max(self.nx, self.ny)), _ptr(out))
+        return out
+
+    def add_noise(self, psi, sigma, seed, inst=0):
+        """psi + sigma xi, xi complex standard normal from the counter-based SplitMix64 stream."""
+        out = self._psi(psi)
+        _load().orc_add_noise(ctypes.byref(self._c), _ptr(out), float(sigma), int(seed) & (2 ** 64 - 1), int(inst))
+        return out
+
+
+def splitmix64(seed, c):
+    """Draw c of the oracle's counter-based SplitMix64 stream `seed`."""
+    return int(_load().orc_splitmix64(int(seed) & (2 ** 64 - 1), int(c)))
 
 
 def fft2(plane, inverse=False):

@@ -38,6 +38,7 @@
 //  * Imaginary time: after each S(dtau) the spinor is rescaled to the target
 //    atom number (Sec. 3.2), either the total (mode 0) or per component
 //    (mode 1).
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -315,6 +316,115 @@ void orc_energy(const orc_model *m, const double *psi, double out[6]) {
   out[4] = w * eram;
   out[5] = w * eint;
   out[0] = out[1] + out[2] + out[3] + out[4] + out[5];
+}
+
+// ---- observables of the spin-Hall ground states (Sec. 6) ----
+
+// Phase-separation parameter (Eq. 14) and circulation (Eq. 15) of one spinor:
+// out = {s, n_up, n_dn, R99}.
+//  * s = 1 - sum rho_up rho_dn / sqrt(sum rho_up^2 sum rho_dn^2), sums over
+//    the grid.  Eq. 14 prints the sum over r outside the bracket of averages;
+//    read (as in the work it cites, and so that s lies in [0, 1]: 0 for
+//    rho_up proportional to rho_dn, 1 for disjoint densities) as the averages
+//    being those sums.
+//  * R99: the radius of the circle about the trap centre (0, 0) that encloses
+//    99 % of the total atom number: radii binned in widths h = min(dx, dy)/2,
+//    R99 = upper edge of the first bin at which the cumulative atom number
+//    reaches 0.99 of the total.
+//  * n_j: winding number of phi_j = arg psi_j around that circle,
+//    counter-clockwise, from `npts` equally spaced points (angles 2 pi k /
+//    npts), psi_j bilinearly interpolated on the periodic grid; the phase
+//    steps wrapped into (-pi, pi] are summed and the sum / 2 pi rounded.  The
+//    circulation of Eq. 15 is 2 pi n_j (hbar = m = 1).
+void orc_observables(const orc_model *m, const double *psi, int npts, double out[4]) {
+  const int nx = m->nx, ny = m->ny;
+  const long n = (long)nx * ny;
+  const double dx = dx_of(m), dy = dy_of(m);
+  const cd *up = reinterpret_cast<const cd *>(psi), *dn = up + n;
+  double a = 0.0, b = 0.0, c = 0.0, tot = 0.0;
+  for (long i = 0; i < n; ++i) {
+    const double ru = std::norm(up[i]), rd = std::norm(dn[i]);
+    a += ru * rd;
+    b += ru * ru;
+    c += rd * rd;
+    tot += ru + rd;
+  }
+  out[0] = 1.0 - a / std::sqrt(b * c);
+  // radial distribution of the total density
+  const double h = 0.5 * std::min(dx, dy);
+  const double rmax = std::sqrt(m->xmax * m->xmax + m->ymax * m->ymax);
+  const int nb = (int)(rmax / h) + 2;
+  std::vector<double> hist(nb, 0.0);
+  for (int iy = 0; iy < ny; ++iy)
+    for (int ix = 0; ix < nx; ++ix) {
+      const double x = -m->xmax + ix * dx, y = -m->ymax + iy * dy;
+      const long i = (long)iy * nx + ix;
+      const int bin = std::min(nb - 1, (int)(std::sqrt(x * x + y * y) / h));
+      hist[bin] += std::norm(up[i]) + std::norm(dn[i]);
+    }
+  double cum = 0.0, R = (nb) * h;
+  for (int k = 0; k < nb; ++k) {
+    cum += hist[k];
+    if (cum >= 0.99 * tot) {
+      R = (k + 1) * h;
+      break;
+    }
+  }
+  out[3] = R;
+  // winding of each component around the circle of radius R
+  auto interp = [&](const cd *f, double x, double y) {
+    const double u = (x + m->xmax) / dx, v = (y + m->ymax) / dy;
+    const double fu = u - std::floor(u), fv = v - std::floor(v);
+    const long i0 = (((long)std::floor(u)) % nx + nx) % nx, j0 = (((long)std::floor(v)) % ny + ny) % ny;
+    const long i1 = (i0 + 1) % nx, j1 = (j0 + 1) % ny;
+    return (1 - fu) * (1 - fv) * f[j0 * nx + i0] + fu * (1 - fv) * f[j0 * nx + i1] +
+           (1 - fu) * fv * f[j1 * nx + i0] + fu * fv * f[j1 * nx + i1];
+  };
+  for (int j = 0; j < 2; ++j) {
+    const cd *f = j == 0 ? up : dn;
+    double total = 0.0;
+    double prev = std::arg(interp(f, R, 0.0));
+    for (int k = 1; k <= npts; ++k) {
+      const double th = 2.0 * kPi * (double)(k % npts) / npts;
+      const double ph = std::arg(interp(f, R * std::cos(th), R * std::sin(th)));
+      double d = ph - prev;
+      while (d > kPi) d -= 2.0 * kPi;
+      while (d <= -kPi) d += 2.0 * kPi;
+      total += d;
+      prev = ph;
+    }
+    out[1 + j] = std::round(total / (2.0 * kPi));
+  }
+}
+
+// ---- annealing noise (Sec. 6: the first imaginary-time segment is
+// periodically perturbed with Gaussian noise) ----
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) as a counter-based generator:
+// draw c of stream `seed` is the output function applied to
+// seed + (c + 1) * 0x9E3779B97F4A7C15.
+unsigned long long orc_splitmix64(unsigned long long seed, unsigned long long c) {
+  unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// psi += sigma xi with xi complex standard normal (E|xi|^2 = 1), independent
+// per element: element e (component-major, then row-major) of instance `inst`
+// takes the draws c = 2 E + 0 and 2 E + 1, E = inst * 2 nx ny + e, as
+// uniforms u = (draw >> 11) 2^-53, and xi = sqrt(-ln(1 - u1)) e^{2 pi i u2}
+// (Box-Muller in polar form).
+void orc_add_noise(const orc_model *m, double *psi, double sigma, unsigned long long seed, long inst) {
+  const long n2 = 2L * m->nx * m->ny;
+  cd *p = reinterpret_cast<cd *>(psi);
+  for (long e = 0; e < n2; ++e) {
+    const unsigned long long E = (unsigned long long)(inst * n2 + e);
+    const double u1 = (double)(orc_splitmix64(seed, 2 * E) >> 11) * 0x1.0p-53;
+    const double u2 = (double)(orc_splitmix64(seed, 2 * E + 1) >> 11) * 0x1.0p-53;
+    const double r = std::sqrt(-std::log(1.0 - u1));
+    p[e] += sigma * r * cd(std::cos(2.0 * kPi * u2), std::sin(2.0 * kPi * u2));
+  }
 }
 
 }  // extern "C"

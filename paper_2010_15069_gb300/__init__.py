@@ -27,8 +27,8 @@ __all__ = [
     "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SPGPE_RELAX_GIVE_UP",
     "SpgpeError",
     "Context", "load",
-    "spgpe_init_grid", "spgpe_init_batch", "spgpe_set_potentials", "spgpe_set_potentials_separable",
-    "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_energy", "spgpe_norm", "spgpe_sync",
+    "spgpe_init_grid", "spgpe_init_batch", "spgpe_init_multi", "spgpe_set_potentials", "spgpe_set_potentials_separable",
+    "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_autotune", "spgpe_observables", "spgpe_add_noise", "spgpe_energy", "spgpe_norm", "spgpe_sync",
     "spgpe_cufft_step_real", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
     "spgpe_last_launches", "spgpe_set_timing", "spgpe_timing",
 ]
@@ -60,6 +60,20 @@ def spgpe_init_batch(nx, ny, xmax, ymax, ninst, dtype=SPGPE_C64, stream=0):
     ctx = ctypes.c_void_p()
     check(load().spgpe_init_batch(ctypes.byref(ctx), int(nx), int(ny), float(xmax), float(ymax),
                                   int(ninst), int(dtype), ctypes.c_void_p(int(stream))))
+    return ctx.value
+
+
+def spgpe_init_multi(classes, dtype=SPGPE_C64, stream=0):
+    """classes: sequence of (nx, ny, ninst, xmax, ymax), one per grid size."""
+    k = len(classes)
+    nx = np.array([c[0] for c in classes], dtype=np.int32)
+    ny = np.array([c[1] for c in classes], dtype=np.int32)
+    ni = np.array([c[2] for c in classes], dtype=np.int32)
+    xm = np.array([c[3] for c in classes], dtype=np.float64)
+    ym = np.array([c[4] for c in classes], dtype=np.float64)
+    ctx = ctypes.c_void_p()
+    check(load().spgpe_init_multi(ctypes.byref(ctx), k, *(a.ctypes.data_as(ctypes.c_void_p) for a in (nx, ny, ni, xm, ym)),
+                                  int(dtype), ctypes.c_void_p(int(stream))))
     return ctx.value
 
 
@@ -99,6 +113,27 @@ def spgpe_relax(ctx, psi_ptr, dtau, tol, max_steps, check_every=200, norm_mode=S
                              int(check_every), int(norm_mode), _ptr(tgt), int(flags), float(handoff), _ptr(res),
                              steps.ctypes.data_as(ctypes.c_void_p)), ctx)
     return res, (int(steps[0]), int(steps[1]))
+
+
+def spgpe_autotune(ctx, psi_ptr, dt, nclass=1):
+    """Returns (chosen variant per class, ms per step per class)."""
+    ch = np.zeros(int(nclass), dtype=np.int32)
+    ms = np.zeros(int(nclass))
+    check(load().spgpe_autotune(ctx, ctypes.c_void_p(int(psi_ptr)), float(dt), ch.ctypes.data_as(ctypes.c_void_p),
+                                _ptr(ms)), ctx)
+    return ch, ms
+
+
+def spgpe_observables(ctx, psi_ptr, ninst=1):
+    """(ninst, 4) array of {s (Eq. 14), n_up, n_dn (Eq. 15 windings), R99}."""
+    out = np.zeros((int(ninst), 4))
+    check(load().spgpe_observables(ctx, ctypes.c_void_p(int(psi_ptr)), _ptr(out)), ctx)
+    return out
+
+
+def spgpe_add_noise(ctx, psi_ptr, sigma, seed):
+    check(load().spgpe_add_noise(ctx, ctypes.c_void_p(int(psi_ptr)), float(sigma),
+                                 ctypes.c_ulonglong(int(seed) & (2 ** 64 - 1))), ctx)
 
 
 def spgpe_energy(ctx, psi_ptr, ninst=1):
@@ -162,16 +197,41 @@ class Context:
     on the host, which the library copies in, steps and copies back.
     """
 
-    def __init__(self, nx, ny, xmax, ymax, dtype="c64", ninst=1, stream=None):
-        self.nx, self.ny, self.ninst = int(nx), int(ny), int(ninst)
+    def __init__(self, nx, ny, xmax, ymax, dtype="c64", ninst=1, stream=None, classes=None):
         self.dtype = {"c64": SPGPE_C64, "c128": SPGPE_C128}[dtype]
         self.np_dtype = np.complex64 if self.dtype == SPGPE_C64 else np.complex128
         self.stream = stream
         s = 0
         if stream is not None:
             s = int(getattr(stream, "cuda_stream", stream))
+        self.classes = None
+        if classes is not None:
+            # multi-size batch: spinors are flat buffers; see class_views()
+            self.classes = [(int(a), int(b), int(n), float(xm), float(ym)) for a, b, n, xm, ym in classes]
+            self.nx = self.ny = None
+            self.ninst = sum(c[2] for c in self.classes)
+            self._ctx = spgpe_init_multi(self.classes, self.dtype, s)
+            return
+        self.nx, self.ny, self.ninst = int(nx), int(ny), int(ninst)
         self._ctx = (spgpe_init_batch(nx, ny, xmax, ymax, ninst, self.dtype, s) if ninst != 1
                      else spgpe_init_grid(nx, ny, xmax, ymax, self.dtype, s))
+
+    @classmethod
+    def multi(cls, classes, dtype="c64", stream=None):
+        """A batch over several grid sizes: classes = [(nx, ny, ninst, xmax, ymax), ...]."""
+        return cls(None, None, None, None, dtype, stream=stream, classes=classes)
+
+    def class_sizes(self):
+        """Complex elements of each class in the flat spinor buffer of a multi-size batch."""
+        return [n * 2 * b * a for a, b, n, _, _ in self.classes]
+
+    def class_views(self, flat):
+        """Views (ninst, 2, ny, nx) of the classes in a flat spinor buffer."""
+        out, o = [], 0
+        for (a, b, n, _, _), sz in zip(self.classes, self.class_sizes()):
+            out.append(flat[o:o + sz].reshape(n, 2, b, a))
+            o += sz
+        return out
 
     @property
     def handle(self):
@@ -195,10 +255,15 @@ class Context:
         self.close()
 
     def _check_psi(self, psi):
-        shape = tuple(psi.shape)
-        want = (2, self.ny, self.nx) if self.ninst == 1 else (self.ninst, 2, self.ny, self.nx)
-        if shape not in (want, (self.ninst, 2, self.ny, self.nx)):
-            raise ValueError(f"spinor shape {shape}, expected {want}")
+        if self.classes is not None:
+            total = sum(self.class_sizes())
+            if tuple(psi.shape) != (total,):
+                raise ValueError(f"a multi-size batch takes a flat spinor of {total} elements")
+        shape = tuple(psi.shape) if self.classes is None else None
+        if shape is not None:
+            want = (2, self.ny, self.nx) if self.ninst == 1 else (self.ninst, 2, self.ny, self.nx)
+            if shape not in (want, (self.ninst, 2, self.ny, self.nx)):
+                raise ValueError(f"spinor shape {shape}, expected {want}")
         if isinstance(psi, np.ndarray):
             if psi.dtype != self.np_dtype or not psi.flags.c_contiguous:
                 raise ValueError(f"host spinor must be C-contiguous {np.dtype(self.np_dtype).name}")
@@ -217,6 +282,13 @@ class Context:
     def set_potentials_separable(self, inst=-1, Vx=None, Vy=None, delta_x=None, delta_y=None, Omega_x=None,
                                  Omega_y=None, g11=0.0, g22=0.0, g12=0.0, kL=0.0):
         nx, ny = self.nx, self.ny
+        if self.classes is not None:
+            first = 0
+            for a, b, n, _, _ in self.classes:
+                if inst == -1 or first <= inst < first + n:
+                    nx, ny = a, b
+                    break
+                first += n
         spgpe_set_potentials_separable(self._ctx, inst, _f64(Vx, nx), _f64(Vy, ny), _f64(delta_x, nx),
                                        _f64(delta_y, ny), _f64(Omega_x, nx), _f64(Omega_y, ny),
                                        g11, g22, g12, kL)
@@ -235,8 +307,18 @@ class Context:
         return spgpe_relax(self._ctx, self._check_psi(psi), dtau, tol, max_steps, check_every, norm_mode, target,
                            flags, handoff, self.ninst)
 
+    def autotune(self, psi, dt):
+        return spgpe_autotune(self._ctx, self._check_psi(psi), dt, 1 if self.classes is None else len(self.classes))
+
     def cufft_step_real(self, psi, dt, nsteps):
         spgpe_cufft_step_real(self._ctx, self._check_psi(psi), dt, nsteps)
+        return psi
+
+    def observables(self, psi):
+        return spgpe_observables(self._ctx, self._check_psi(psi), self.ninst)
+
+    def add_noise(self, psi, sigma, seed):
+        spgpe_add_noise(self._ctx, self._check_psi(psi), sigma, seed)
         return psi
 
     def energy(self, psi):

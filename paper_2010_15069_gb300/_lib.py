@@ -23,6 +23,7 @@ _P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 SIGNATURES = {
     "spgpe_init_grid": (_I, [ctypes.POINTER(_P), _I, _I, _D, _D, _I, _P]),
     "spgpe_init_batch": (_I, [ctypes.POINTER(_P), _I, _I, _D, _D, _I, _I, _P]),
+    "spgpe_init_multi": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _I, _P]),
     "spgpe_set_potentials": (_I, [_P, _P, _P, _P, _D, _D, _D, _D]),
     "spgpe_set_potentials_separable": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _D, _D, _D, _D]),
     "spgpe_step_real": (_I, [_P, _P, _D, _I]),
@@ -39,6 +40,9 @@ SIGNATURES = {
     "spgpe_timing": (_I, [_P, _P, _P]),
     "spgpe_norm_noalloc": (_I, [_P, _I, _I, _I, _D, _D, _I, _P, _P]),
     "spgpe_relax": (_I, [_P, _P, _D, _D, _I, _I, _I, _P, _I, _D, _P, _P]),
+    "spgpe_autotune": (_I, [_P, _P, _D, _P, _P]),
+    "spgpe_observables": (_I, [_P, _P, _P]),
+    "spgpe_add_noise": (_I, [_P, _P, _D, ctypes.c_ulonglong]),
 }
 NKINDS = 9
 KIND_NAMES = ["row_real_open", "row_real_fused", "row_real_close", "col_real", "row_imag_open",

@@ -58,6 +58,8 @@ struct spgpe_ctx {
   bool use_active = false;
   void *d_scratch = nullptr;  // psi-sized: energy transform / residual previous state
   void *d_stage = nullptr;    // psi-sized: staging of host spinors
+  double *d_obs = nullptr;    // observables: radial histogram, radii, windings
+  size_t n_obs = 0;
   double tab_dt = NAN;
   int tab_imag = -1;
   int omega_pieces = 0;
@@ -83,6 +85,18 @@ struct spgpe_ctx {
   CUtensorMap map{};
   void *d_gparT = nullptr;
 
+  // Batch over several grid sizes: the size classes are child contexts, each
+  // on a stream of its own; this context only dispatches to them.  Class k
+  // holds global instances cls_first[k] .. cls_first[k] + ninst_k - 1 at byte
+  // offset cls_off[k] of the spinor buffer.
+  std::vector<spgpe_ctx *> cls;
+  std::vector<int> cls_first;
+  std::vector<size_t> cls_off;
+  size_t multi_bytes = 0;
+  cudaEvent_t fork_ev = nullptr;  // parent: recorded on its stream before the classes start
+  cudaEvent_t join_ev = nullptr;  // child: recorded on its stream when its work is queued
+  bool own_stream = false;        // child: the stream was created by the library
+
   std::string err;
   int last_launches = 0;
 
@@ -91,7 +105,7 @@ struct spgpe_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
 
-  size_t psi_bytes() const { return (size_t)ninst * 2 * nx * ny * es; }
+  size_t psi_bytes() const { return cls.empty() ? (size_t)ninst * 2 * nx * ny * es : multi_bytes; }
   long plane() const { return (long)nx * ny; }
 };
 
@@ -157,10 +171,19 @@ void free_all(spgpe_ctx *c) {
     if (p) cudaFree(p);
   if (c->plan_ok) cufftDestroy(c->plan);
   if (c->d_psi64) cudaFree(c->d_psi64);
+  if (c->d_obs) cudaFree(c->d_obs);
   if (c->twin) {
     free_all(c->twin);
     delete c->twin;
   }
+  for (spgpe_ctx *k : c->cls) {
+    cudaStreamSynchronize(k->st);
+    free_all(k);
+    delete k;
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
 }
 
 // Twiddle table of the block FFT plan for n = 2^logn points with 2^loge
@@ -486,6 +509,8 @@ cudaError_t col(spgpe_ctx *c, bool imag, const ColArgs &a) {
 
 int check_ready(spgpe_ctx *c) {
   if (!c) return SPGPE_EINVAL;
+  for (spgpe_ctx *k : c->cls)
+    if (check_ready(k)) return fail(c, SPGPE_ESTATE, "potentials not set for every instance");
   for (char s : c->inst_set)
     if (!s) return fail(c, SPGPE_ESTATE, "potentials not set for every instance");
   return SPGPE_OK;
@@ -667,6 +692,62 @@ int imag_collect(spgpe_ctx *c, double dtau, double *residual_out) {
   return SPGPE_OK;
 }
 
+// Size classes of a multi-size batch: start them after the work already on
+// the caller's stream, and make the caller's stream wait for what they queue.
+int fork_classes(spgpe_ctx *c) {
+  CK(c, cudaEventRecord(c->fork_ev, c->st));
+  for (spgpe_ctx *k : c->cls) CK(c, cudaStreamWaitEvent(k->st, c->fork_ev, 0));
+  return SPGPE_OK;
+}
+
+int join_classes(spgpe_ctx *c) {
+  for (spgpe_ctx *k : c->cls) {
+    CK(c, cudaEventRecord(k->join_ev, k->st));
+    CK(c, cudaStreamWaitEvent(c->st, k->join_ev, 0));
+  }
+  return SPGPE_OK;
+}
+
+// A class's failure, reported by the batch.
+int class_fail(spgpe_ctx *c, spgpe_ctx *k, int r) { return fail(c, r, k->err); }
+
+// Class of a global instance index (-1 when out of range).
+int class_of(const spgpe_ctx *c, int inst) {
+  for (size_t k = 0; k < c->cls.size(); ++k)
+    if (inst >= c->cls_first[k] && inst < c->cls_first[k] + c->cls[k]->ninst) return (int)k;
+  return -1;
+}
+
+// Run `call(class, class spinor, first instance)` for every class of a
+// multi-size batch between a fork and a join on the caller's stream; a host
+// spinor is staged once for the whole batch.
+template <class F> int for_classes(spgpe_ctx *c, const void *psi, bool write_back, F &&call) {
+  void *p;
+  bool host;
+  int r = begin_psi(c, psi, &p, &host);
+  if (r) return r;
+  if ((r = fork_classes(c))) return r;
+  int launches = 0;
+  for (size_t k = 0; k < c->cls.size(); ++k) {
+    r = call(c->cls[k], static_cast<char *>(p) + c->cls_off[k], c->cls_first[k]);
+    launches += c->cls[k]->last_launches;
+    if (r) return class_fail(c, c->cls[k], r);
+  }
+  if ((r = join_classes(c))) return r;
+  c->last_launches = launches;
+  if (host) {
+    // a host spinor makes the call synchronous: report device-side errors now
+    if (write_back) {
+      if ((r = end_psi(c, const_cast<void *>(psi), true))) return r;
+    } else {
+      CK(c, cudaStreamSynchronize(c->st));
+    }
+    for (spgpe_ctx *k : c->cls)
+      if ((r = read_flags(k))) return class_fail(c, k, r);
+  }
+  return SPGPE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -686,6 +767,71 @@ int spgpe_init_batch(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, 
   return init_common(out, nx, ny, xmax, ymax, ninst, dtype, stream);
 }
 
+int spgpe_init_multi(spgpe_ctx **out, int nclass, const int *nx, const int *ny, const int *ninst,
+                     const double *xmax, const double *ymax, int dtype, void *stream) {
+  if (!out) return fail(nullptr, SPGPE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nclass < 1 || nclass > 64 || !nx || !ny || !ninst || !xmax || !ymax)
+    return fail(nullptr, SPGPE_EINVAL, "nclass must be in [1, 64] and the arrays non-NULL");
+  if (dtype != SPGPE_C64 && dtype != SPGPE_C128) return fail(nullptr, SPGPE_EINVAL, "dtype must be SPGPE_C64 or SPGPE_C128");
+  long total = 0;
+  double work = 0.0;
+  for (int k = 0; k < nclass; ++k) {
+    if (!pow2_in_range(nx[k]) || !pow2_in_range(ny[k]))
+      return fail(nullptr, SPGPE_EINVAL, "nx and ny must be powers of two in [8, 4096]");
+    if (!(std::isfinite(xmax[k]) && xmax[k] > 0 && std::isfinite(ymax[k]) && ymax[k] > 0))
+      return fail(nullptr, SPGPE_EINVAL, "xmax and ymax must be finite and positive");
+    if (ninst[k] < 1 || ninst[k] > 65535) return fail(nullptr, SPGPE_EINVAL, "ninst must be in [1, 65535]");
+    total += ninst[k];
+    work += (double)ninst[k] * nx[k] * ny[k];
+  }
+  if (total > 65535) return fail(nullptr, SPGPE_EINVAL, "at most 65535 instances in all");
+  spgpe_ctx *c = new (std::nothrow) spgpe_ctx();
+  if (!c) return fail(nullptr, SPGPE_ENOMEM, "host allocation failed");
+  c->dtype = dtype;
+  c->es = dtype == SPGPE_C64 ? 8 : 16;
+  c->ninst = (int)total;
+  c->st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 0;
+  cudaGetLastError();
+  auto bail = [&](int code, const std::string &msg) {
+    free_all(c);
+    delete c;
+    return fail(nullptr, code, msg);
+  };
+  if (cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return bail(SPGPE_ECUDA, "cudaEventCreate failed");
+  size_t off = 0;
+  int first = 0;
+  for (int k = 0; k < nclass; ++k) {
+    cudaStream_t ks = nullptr;
+    if (cudaStreamCreateWithFlags(&ks, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(SPGPE_ECUDA, "cudaStreamCreate failed");
+    spgpe_ctx *kc = nullptr;
+    const int r = init_common(&kc, nx[k], ny[k], xmax[k], ymax[k], ninst[k], dtype, ks);
+    if (r) {
+      cudaStreamDestroy(ks);
+      return bail(r, g_init_error);
+    }
+    kc->own_stream = true;
+    c->cls.push_back(kc);
+    if (cudaEventCreateWithFlags(&kc->join_ev, cudaEventDisableTiming) != cudaSuccess)
+      return bail(SPGPE_ECUDA, "cudaEventCreate failed");
+    // the persistent passes of the classes share the GPU in proportion to their points
+    if (sms > 0) kc->sms = std::max(1, (int)std::lround(sms * (double)ninst[k] * nx[k] * ny[k] / work));
+    c->cls_first.push_back(first);
+    c->cls_off.push_back(off);
+    first += ninst[k];
+    off += kc->psi_bytes();
+  }
+  c->multi_bytes = off;
+  c->sms = sms;
+  *out = c;
+  return SPGPE_OK;
+}
+
 void spgpe_destroy(spgpe_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
@@ -695,6 +841,12 @@ void spgpe_destroy(spgpe_ctx *c) {
 
 int spgpe_set_potentials(spgpe_ctx *c, const double *V, const double *delta, const double *Omega, double g11,
                          double g22, double g12, double kL) {
+  if (c && c->cls.size() > 1)
+    return fail(c, SPGPE_EINVAL, "2D potential arrays need one grid size; set a multi-size batch per instance");
+  if (c && c->cls.size() == 1) {
+    const int r = spgpe_set_potentials(c->cls[0], V, delta, Omega, g11, g22, g12, kL);
+    return r ? class_fail(c, c->cls[0], r) : r;
+  }
   if (!c) return SPGPE_EINVAL;
   const size_t n = (size_t)c->nx * c->ny;
   if (!all_finite(V, n) || !all_finite(delta, n) || !all_finite(Omega, n))
@@ -730,6 +882,24 @@ int spgpe_set_potentials(spgpe_ctx *c, const double *V, const double *delta, con
 int spgpe_set_potentials_separable(spgpe_ctx *c, int inst, const double *Vx, const double *Vy, const double *delta_x,
                                    const double *delta_y, const double *Omega_x, const double *Omega_y, double g11,
                                    double g22, double g12, double kL) {
+  if (c && !c->cls.empty()) {
+    if (inst == -1) {
+      for (spgpe_ctx *k : c->cls)
+        if (k->nx != c->cls[0]->nx || k->ny != c->cls[0]->ny)
+          return fail(c, SPGPE_EINVAL, "inst = -1 needs one grid size; set a multi-size batch per instance");
+      for (spgpe_ctx *k : c->cls) {
+        const int r = spgpe_set_potentials_separable(k, -1, Vx, Vy, delta_x, delta_y, Omega_x, Omega_y, g11, g22,
+                                                     g12, kL);
+        if (r) return class_fail(c, k, r);
+      }
+      return SPGPE_OK;
+    }
+    const int k = class_of(c, inst);
+    if (k < 0) return fail(c, SPGPE_EINVAL, "instance index out of range");
+    const int r = spgpe_set_potentials_separable(c->cls[(size_t)k], inst - c->cls_first[(size_t)k], Vx, Vy, delta_x,
+                                                 delta_y, Omega_x, Omega_y, g11, g22, g12, kL);
+    return r ? class_fail(c, c->cls[(size_t)k], r) : r;
+  }
   if (!c) return SPGPE_EINVAL;
   if (inst < -1 || inst >= c->ninst) return fail(c, SPGPE_EINVAL, "instance index out of range");
   const int nx = c->nx, ny = c->ny;
@@ -770,6 +940,12 @@ int spgpe_set_potentials_separable(spgpe_ctx *c, int inst, const double *Vx, con
 }
 
 int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
+  if (c && !c->cls.empty()) {
+    if (!psi || nsteps < 0 || !std::isfinite(dt)) return fail(c, SPGPE_EINVAL, "bad psi, dt or nsteps");
+    int r = check_ready(c);
+    if (r) return r;
+    return for_classes(c, psi, true, [&](spgpe_ctx *k, void *p, int) { return spgpe_step_real(k, p, dt, nsteps); });
+  }
   int r = check_ready(c);
   if (r) return r;
   c->last_launches = 0;
@@ -792,6 +968,34 @@ int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
 
 int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_mode, const double *target,
                     double *residual_out) {
+  if (c && !c->cls.empty()) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!psi || nsteps < 0 || !std::isfinite(dtau)) return fail(c, SPGPE_EINVAL, "bad psi, dtau or nsteps");
+    if (norm_mode != SPGPE_NORM_TOTAL && norm_mode != SPGPE_NORM_PER_COMPONENT)
+      return fail(c, SPGPE_EINVAL, "bad norm_mode");
+    const double t0 = target ? target[0] : 0.5, t1 = target ? target[1] : 0.5;
+    if (!(std::isfinite(t0) && std::isfinite(t1) && t0 >= 0 && t1 >= 0 && t0 + t1 > 0))
+      return fail(c, SPGPE_EINVAL, "targets must be finite, non-negative, not both zero");
+    if (nsteps == 0) {
+      if (residual_out)
+        for (int i = 0; i < c->ninst; ++i) residual_out[i] = NAN;
+      return SPGPE_OK;
+    }
+    // queue every class before reading any residual, so the classes overlap
+    r = for_classes(c, psi, true, [&](spgpe_ctx *k, void *p, int) {
+      k->last_launches = 0;
+      return imag_enqueue(k, p, dtau, nsteps, norm_mode, t0, t1, residual_out != nullptr);
+    });
+    if (r) return r;
+    if (residual_out)
+      for (size_t k = 0; k < c->cls.size(); ++k)
+        if ((r = imag_collect(c->cls[k], dtau, residual_out + c->cls_first[k]))) return class_fail(c, c->cls[k], r);
+    if (residual_out)
+      for (spgpe_ctx *k : c->cls)
+        if ((r = read_flags(k))) return class_fail(c, k, r);
+    return SPGPE_OK;
+  }
   int r = check_ready(c);
   if (r) return r;
   c->last_launches = 0;
@@ -817,6 +1021,8 @@ int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_m
 }
 
 int spgpe_set_timing(spgpe_ctx *c, int enable) {
+  if (c)
+    for (spgpe_ctx *k : c->cls) spgpe_set_timing(k, enable);
   if (!c) return SPGPE_EINVAL;
   c->timing = enable != 0;
   return SPGPE_OK;
@@ -824,6 +1030,23 @@ int spgpe_set_timing(spgpe_ctx *c, int enable) {
 
 int spgpe_timing(spgpe_ctx *c, double *ms_out, int *count_out) {
   if (!c || !ms_out || !count_out) return SPGPE_EINVAL;
+  if (!c->cls.empty()) {
+    std::vector<double> ms(SPGPE_NKINDS);
+    std::vector<int> cnt(SPGPE_NKINDS);
+    for (int k = 0; k < SPGPE_NKINDS; ++k) {
+      ms_out[k] = 0.0;
+      count_out[k] = 0;
+    }
+    for (spgpe_ctx *k : c->cls) {
+      const int r = spgpe_timing(k, ms.data(), cnt.data());
+      if (r) return class_fail(c, k, r);
+      for (int j = 0; j < SPGPE_NKINDS; ++j) {
+        ms_out[j] += ms[(size_t)j];
+        count_out[j] += cnt[(size_t)j];
+      }
+    }
+    return SPGPE_OK;
+  }
   CK(c, cudaStreamSynchronize(c->st));
   for (int k = 0; k < SPGPE_NKINDS; ++k) {
     ms_out[k] = 0.0;
@@ -843,12 +1066,24 @@ int spgpe_timing(spgpe_ctx *c, double *ms_out, int *count_out) {
 
 int spgpe_sync(spgpe_ctx *c) {
   if (!c) return SPGPE_EINVAL;
+  if (!c->cls.empty()) {
+    CK(c, cudaStreamSynchronize(c->st));
+    for (spgpe_ctx *k : c->cls) {
+      const int r = spgpe_sync(k);
+      if (r) return class_fail(c, k, r);
+    }
+    return SPGPE_OK;
+  }
   CK(c, cudaStreamSynchronize(c->st));
   return read_flags(c);
 }
 
 int spgpe_norm(spgpe_ctx *c, const void *psi, double *out) {
   if (!c || !psi || !out) return fail(c, SPGPE_EINVAL, "NULL argument");
+  if (!c->cls.empty())
+    return for_classes(c, psi, false, [&](spgpe_ctx *k, void *p, int first) {
+      return spgpe_norm(k, p, out + 2 * (size_t)first);
+    });
   void *p;
   bool host;
   int r = begin_psi(c, psi, &p, &host);
@@ -877,6 +1112,10 @@ int spgpe_energy(spgpe_ctx *c, const void *psi, double *out) {
   int r = check_ready(c);
   if (r) return r;
   if (!psi || !out) return fail(c, SPGPE_EINVAL, "NULL argument");
+  if (!c->cls.empty())
+    return for_classes(c, psi, false, [&](spgpe_ctx *k, void *p, int first) {
+      return spgpe_energy(k, p, out + 6 * (size_t)first);
+    });
   if ((r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
   void *p;
   bool host;
@@ -924,6 +1163,12 @@ int spgpe_energy(spgpe_ctx *c, const void *psi, double *out) {
 }
 
 int spgpe_cufft_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
+  if (c && !c->cls.empty()) {
+    if (!psi || !is_device_ptr(psi)) return fail(c, SPGPE_EINVAL, "the comparator takes device spinors only");
+    return for_classes(c, psi, false, [&](spgpe_ctx *k, void *p, int) {
+      return spgpe_cufft_step_real(k, p, dt, nsteps);
+    });
+  }
   int r = check_ready(c);
   if (r) return r;
   c->last_launches = 0;
@@ -1001,62 +1246,162 @@ int ensure_twin(spgpe_ctx *c) {
   return dev_alloc(c, &c->d_psi64, t->psi_bytes());
 }
 
+// A context that owns kernels (a single-size context, a size class of a
+// multi-size batch, or their complex64 twins), its device spinor and the
+// global index of its first instance.
+struct Member {
+  spgpe_ctx *c;
+  void *p;
+  int first;
+};
+
 // Imaginary-time steps in chunks of `check`, each ending with the residual of
 // its last step, until every instance is within tol or max_steps have run.
-// An instance that is done is frozen (the passes skip it) while the others
-// go on; its residual stays the last one measured.  to_floor: an instance is
-// also done once its residual has reached the rounding floor of complex64
-// (below 2^-18 / dtau) and improves by less than a fifth from one chunk to
-// the next.  give_up: an instance is also done once its smallest residual so
-// far has not dropped by 1 % in kStallChecks chunks (a metastable state).
+// The members' chunks are queued on their own streams before any residual is
+// read, so size classes run side by side.  An instance that is done is frozen
+// (the passes skip it) while the others go on; its residual stays the last
+// one measured.  to_floor: an instance is also done once its residual has
+// reached the rounding floor of complex64 (below 2^-18 / dtau) and improves by
+// less than a fifth from one chunk to the next.  give_up: an instance is also
+// done once its smallest residual so far has not halved in kStallChecks
+// chunks (a metastable state, or a relaxation far too slow for the budget).
 constexpr int kStallChecks = 40;
-int relax_stage(spgpe_ctx *c, void *p, double dtau, double tol, int max_steps, int check, int norm_mode,
-                const double *target, bool to_floor, bool give_up, std::vector<double> &res, int *steps,
-                int *launches) {
+int relax_stage(spgpe_ctx *owner, std::vector<Member> &mem, int ntotal, double dtau, double tol, int max_steps,
+                int check, int norm_mode, double t0, double t1, bool to_floor, bool give_up,
+                std::vector<double> &res, int *steps, int *launches) {
   const double floor64 = std::ldexp(1.0, -18) / dtau;
-  const int ni = c->ninst;
-  std::vector<int> act((size_t)ni, 1), since((size_t)ni, 0);
-  std::vector<double> prev((size_t)ni, INFINITY), best((size_t)ni, INFINITY), r((size_t)ni);
-  int done = 0, nact = ni;
-  CK(c, cudaMemcpyAsync(c->d_active, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
-  c->use_active = true;
+  std::vector<int> act((size_t)ntotal, 1), since((size_t)ntotal, 0);
+  std::vector<double> prev((size_t)ntotal, INFINITY), best((size_t)ntotal, INFINITY), r((size_t)ntotal);
+  int done = 0, nact = ntotal;
+  auto upload_mask = [&](const Member &m) {
+    return cudaMemcpyAsync(m.c->d_active, act.data() + m.first, (size_t)m.c->ninst * sizeof(int),
+                           cudaMemcpyHostToDevice, m.c->st);
+  };
   auto finish = [&](int code) {
-    c->use_active = false;
+    for (Member &m : mem) m.c->use_active = false;
     *steps = done;
     return code;
   };
+  for (Member &m : mem) {
+    const cudaError_t e = upload_mask(m);
+    if (e != cudaSuccess) return finish(cuda_fail(owner, e, "active mask upload"));
+    m.c->use_active = true;
+  }
+  // Chunks after the first are replayed from a CUDA graph of the whole chunk
+  // (every member, forked from and joined into the owner's stream); the
+  // frozen-instance mask is read from device memory, so the graph stays valid.
+  const bool multi = !owner->cls.empty();
+  const cudaStream_t os = multi ? owner->st : mem[0].c->st;
+  bool timing = false;
+  for (Member &m : mem) timing = timing || m.c->timing;
+  cudaGraphExec_t exec = nullptr;
+  int graph_launches = 0;
+  // the legacy and per-thread default streams cannot be captured
+  bool use_graph = os != nullptr && os != cudaStreamLegacy && os != cudaStreamPerThread;
+  auto enqueue = [&](int n) -> int {
+    int rc;
+    if (multi && (rc = fork_classes(owner))) return rc;
+    for (Member &m : mem) {
+      m.c->last_launches = 0;
+      if ((rc = imag_enqueue(m.c, m.p, dtau, n, norm_mode, t0, t1, true))) return fail(owner, rc, m.c->err);
+      graph_launches += m.c->last_launches;
+    }
+    if (multi && (rc = join_classes(owner))) return rc;
+    return SPGPE_OK;
+  };
+  auto drop_graph = [&] {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  };
   while (done < max_steps && nact > 0) {
     const int n = std::min(check, max_steps - done);
-    const int rc = spgpe_step_imag(c, p, dtau, n, norm_mode, target, r.data());
-    if (rc) return finish(rc);
-    *launches += c->last_launches;
+    int rc = SPGPE_OK;
+    if (done > 0 && n == check && !timing && use_graph && !exec) {
+      // capture one chunk (tables, scratch and launch attributes are in place
+      // after the first); if capture is refused, run the chunks directly
+      cudaGraph_t g = nullptr;
+      graph_launches = 0;
+      bool ok = cudaStreamBeginCapture(os, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      if (ok) {
+        const int rc0 = enqueue(n);
+        ok = cudaStreamEndCapture(os, &g) == cudaSuccess && rc0 == SPGPE_OK && g &&
+             cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+      }
+      if (!ok) {
+        drop_graph();
+        use_graph = false;
+        cudaGetLastError();
+        owner->err.clear();
+      }
+    }
+    if (exec && n == check) {
+      const cudaError_t e = cudaGraphLaunch(exec, os);
+      if (e != cudaSuccess) {
+        drop_graph();
+        return finish(cuda_fail(owner, e, "cudaGraphLaunch"));
+      }
+      *launches += graph_launches;
+      if (multi) {
+        const cudaError_t e3 = cudaStreamSynchronize(os);  // the members' streams read what the graph wrote
+        if (e3 != cudaSuccess) {
+          drop_graph();
+          return finish(cuda_fail(owner, e3, "chunk graph"));
+        }
+      }
+    } else {
+      graph_launches = 0;
+      rc = enqueue(n);
+      *launches += graph_launches;
+      if (rc) {
+        drop_graph();
+        return finish(rc);
+      }
+    }
+    for (Member &m : mem) {
+      rc = imag_collect(m.c, dtau, r.data() + m.first);
+      if (!rc) rc = read_flags(m.c);
+      if (rc) {
+        drop_graph();
+        return finish(fail(owner, rc, m.c->err));
+      }
+    }
     done += n;
-    bool changed = false;
-    for (int i = 0; i < ni; ++i) {
-      if (!act[(size_t)i]) continue;
-      const double v = std::isnan(r[(size_t)i]) ? INFINITY : r[(size_t)i];
-      res[(size_t)i] = v;
-      if (v < 0.99 * best[(size_t)i]) {
-        best[(size_t)i] = v;
-        since[(size_t)i] = 0;
-      } else {
-        ++since[(size_t)i];
+    std::vector<char> changed(mem.size(), 0);
+    for (size_t k = 0; k < mem.size(); ++k)
+      for (int j = 0; j < mem[k].c->ninst; ++j) {
+        const size_t i = (size_t)(mem[k].first + j);
+        if (!act[i]) continue;
+        const double v = std::isnan(r[i]) ? INFINITY : r[i];
+        res[i] = v;
+        if (v < 0.5 * best[i]) {
+          best[i] = v;
+          since[i] = 0;
+        } else {
+          ++since[i];
+        }
+        if (v <= tol || (to_floor && v < floor64 && v > 0.8 * prev[i]) || (give_up && since[i] >= kStallChecks)) {
+          act[i] = 0;
+          --nact;
+          changed[k] = 1;
+        }
+        prev[i] = v;
       }
-      if (v <= tol || (to_floor && v < floor64 && v > 0.8 * prev[(size_t)i]) ||
-          (give_up && since[(size_t)i] >= kStallChecks)) {
-        act[(size_t)i] = 0;
-        --nact;
-        changed = true;
-      }
-      prev[(size_t)i] = v;
-    }
-    if (changed && nact > 0) {
-      // a pageable-memory copy: the host array is consumed before the call returns
-      const cudaError_t e = cudaMemcpyAsync(c->d_active, act.data(), act.size() * sizeof(int),
-                                            cudaMemcpyHostToDevice, c->st);
-      if (e != cudaSuccess) return finish(cuda_fail(c, e, "active mask upload"));
-    }
+    if (nact > 0)
+      for (size_t k = 0; k < mem.size(); ++k)
+        if (changed[k]) {
+          // a pageable-memory copy: the host array is consumed before the call
+          // returns; a multi-size batch's graph runs on another stream, so the
+          // copy must also have landed
+          cudaError_t e = upload_mask(mem[k]);
+          if (e == cudaSuccess && multi) e = cudaStreamSynchronize(mem[k].c->st);
+          if (e != cudaSuccess) {
+            drop_graph();
+            return finish(cuda_fail(owner, e, "active mask upload"));
+          }
+        }
   }
+  drop_graph();
   return finish(SPGPE_OK);
 }
 
@@ -1072,27 +1417,48 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
       !(handoff >= 0) || !std::isfinite(handoff))
     return fail(c, SPGPE_EINVAL, "bad psi, dtau, tol, max_steps, check_every or handoff");
   if (flags & ~(SPGPE_RELAX_LADDER | SPGPE_RELAX_GIVE_UP)) return fail(c, SPGPE_EINVAL, "unknown flags");
+  if (norm_mode != SPGPE_NORM_TOTAL && norm_mode != SPGPE_NORM_PER_COMPONENT)
+    return fail(c, SPGPE_EINVAL, "bad norm_mode");
+  const double t0 = target ? target[0] : 0.5, t1 = target ? target[1] : 0.5;
+  if (!(std::isfinite(t0) && std::isfinite(t1) && t0 >= 0 && t1 >= 0 && t0 + t1 > 0))
+    return fail(c, SPGPE_EINVAL, "targets must be finite, non-negative, not both zero");
   const bool ladder = (flags & SPGPE_RELAX_LADDER) && c->dtype == SPGPE_C128;
   const bool give_up = (flags & SPGPE_RELAX_GIVE_UP) != 0;
   void *p;
   bool host;
   if ((r = begin_psi(c, psi, &p, &host))) return r;
+  std::vector<Member> mem;
+  if (c->cls.empty()) {
+    mem.push_back({c, p, 0});
+  } else {
+    if ((r = fork_classes(c))) return r;
+    for (size_t k = 0; k < c->cls.size(); ++k)
+      mem.push_back({c->cls[k], static_cast<char *>(p) + c->cls_off[k], c->cls_first[k]});
+  }
   std::vector<double> res((size_t)c->ninst, NAN);
   int s64 = 0, s = 0, launches = 0;
   if (ladder) {
-    if ((r = ensure_twin(c))) return r;
-    const long n = (long)c->ninst * 2 * c->plane();
-    CK(c, launch_convert(p, 16, c->d_psi64, 8, n, c->sms, c->st));
+    std::vector<Member> m64;
+    for (Member &m : mem) {
+      if ((r = ensure_twin(m.c))) return fail(c, r, m.c->err);
+      CK(c, launch_convert(m.p, 16, m.c->d_psi64, 8, (long)m.c->ninst * 2 * m.c->plane(), m.c->sms, m.c->st));
+      m64.push_back({m.c->twin, m.c->d_psi64, m.first});
+      ++launches;
+    }
     // complex64 down to the hand-off residual, or (handoff = 0) its rounding floor
-    r = relax_stage(c->twin, c->d_psi64, dtau, std::max(tol, handoff), max_steps, check_every, norm_mode, target,
+    r = relax_stage(c, m64, c->ninst, dtau, std::max(tol, handoff), max_steps, check_every, norm_mode, t0, t1,
                     handoff == 0.0, give_up, res, &s64, &launches);
-    if (r) return fail(c, r, "complex64 stage: " + c->twin->err);
-    CK(c, launch_convert(c->d_psi64, 8, p, 16, n, c->sms, c->st));
-    launches += 2;
+    if (r) return r;
+    for (Member &m : mem) {
+      CK(c, launch_convert(m.c->d_psi64, 8, m.p, 16, (long)m.c->ninst * 2 * m.c->plane(), m.c->sms, m.c->st));
+      ++launches;
+    }
   }
-  // the context's own steps (the staged host spinor is already on the device)
-  r = relax_stage(c, p, dtau, tol, max_steps, check_every, norm_mode, target, false, give_up, res, &s, &launches);
+  // the context's own precision (a staged host spinor is already on the device)
+  r = relax_stage(c, mem, c->ninst, dtau, tol, max_steps, check_every, norm_mode, t0, t1, false, give_up, res, &s,
+                  &launches);
   if (r) return r;
+  if (!c->cls.empty() && (r = join_classes(c))) return r;
   c->last_launches = launches;
   if ((r = end_psi(c, psi, host))) return r;
   if (residual_out)
@@ -1102,4 +1468,172 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
     steps_out[1] = s;
   }
   return SPGPE_OK;
+}
+
+// ------------------------------------------------------------- autotuning
+
+extern "C" int spgpe_autotune(spgpe_ctx *c, const void *psi, double dt, int *choice_out, double *ms_out) {
+  int r = check_ready(c);
+  if (r) return r;
+  if (!psi || !std::isfinite(dt)) return fail(c, SPGPE_EINVAL, "bad psi or dt");
+  void *p;
+  bool host;
+  if ((r = begin_psi(c, psi, &p, &host))) return r;
+  std::vector<Member> mem;
+  if (c->cls.empty()) {
+    mem.push_back({c, p, 0});
+  } else {
+    CK(c, cudaStreamSynchronize(c->st));  // the spinor's producers are done before the classes copy it
+    for (size_t k = 0; k < c->cls.size(); ++k)
+      mem.push_back({c->cls[k], static_cast<char *>(p) + c->cls_off[k], c->cls_first[k]});
+  }
+  constexpr int kWarm = 2, kTimed = 8;
+  for (size_t k = 0; k < mem.size(); ++k) {
+    spgpe_ctx *m = mem[k].c;
+    if ((r = dev_alloc(m, &m->d_scratch, m->psi_bytes()))) return fail(c, r, m->err);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = INFINITY;
+    for (int v = 0; v < 4 && !r; ++v) {
+      // variant v: bit 0 persistent row pass, bit 1 persistent column pass
+      m->persistent_row = (v & 1) != 0;
+      m->persistent_col = (v & 2) != 0;
+      cudaError_t e = cudaMemcpyAsync(m->d_scratch, mem[k].p, m->psi_bytes(), cudaMemcpyDeviceToDevice, m->st);
+      if (e != cudaSuccess) {
+        r = cuda_fail(c, e, "autotune copy");
+        break;
+      }
+      if ((r = spgpe_step_real(m, m->d_scratch, dt, kWarm))) break;
+      float ms = 0.f;
+      if ((e = cudaEventRecord(e0, m->st)) != cudaSuccess ||
+          ((r = spgpe_step_real(m, m->d_scratch, dt, kTimed)) == SPGPE_OK &&
+           ((e = cudaEventRecord(e1, m->st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess))) {
+        r = cuda_fail(c, e, "autotune timing");
+        break;
+      }
+      if (r) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) return r == SPGPE_ECUDA ? r : fail(c, r, m->err);
+    m->persistent_row = (best & 1) != 0;
+    m->persistent_col = (best & 2) != 0;
+    if (m->twin) {
+      m->twin->persistent_row = m->persistent_row;
+      m->twin->persistent_col = m->persistent_col;
+    }
+    if (choice_out) choice_out[k] = best;
+    if (ms_out) ms_out[k] = best_ms / kTimed;
+  }
+  if (host) CK(c, cudaStreamSynchronize(c->st));
+  return SPGPE_OK;
+}
+
+// ------------------------------------------- Sec. 6 observables and noise
+
+namespace {
+
+int observables_one(spgpe_ctx *c, void *p, double *out) {
+  ObsGeom g;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.xmax = c->xmax;
+  g.ymax = c->ymax;
+  g.dx = c->dx;
+  g.dy = c->dy;
+  g.h = 0.5 * std::min(c->dx, c->dy);
+  g.nb = (int)(std::sqrt(c->xmax * c->xmax + c->ymax * c->ymax) / g.h) + 2;
+  const int ni = c->ninst, sb = 128, npts = 4 * std::max(c->nx, c->ny);
+  // [ninst][nb] histogram, then R [ninst] and windings [ninst][2]
+  const size_t need = (size_t)ni * ((size_t)g.nb + 3);
+  if (c->n_obs < need) {
+    if (c->d_obs) cudaFree(c->d_obs);
+    c->d_obs = nullptr;
+    c->n_obs = 0;
+    const int r = dev_alloc(c, (void **)&c->d_obs, need * sizeof(double));
+    if (r) return r;
+    c->n_obs = need;
+  }
+  double *hist = c->d_obs, *dR = hist + (size_t)ni * g.nb, *dw = dR + ni;
+  CK(c, cudaMemsetAsync(hist, 0, (size_t)ni * g.nb * sizeof(double), c->st));
+  CK(c, launch_observables((int)c->es, p, g, ni, c->d_partials, sb, hist, nullptr, npts, nullptr, 0, c->st));
+  std::vector<double> part((size_t)ni * sb * 4), h((size_t)ni * g.nb);
+  CK(c, cudaMemcpyAsync(part.data(), c->d_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  std::vector<double> R((size_t)ni);
+  for (int i = 0; i < ni; ++i) {
+    double a = 0, b = 0, cc = 0, tot = 0;
+    for (int k = 0; k < sb; ++k) {
+      const double *q = &part[((size_t)i * sb + k) * 4];
+      a += q[0];
+      b += q[1];
+      cc += q[2];
+      tot += q[3];
+    }
+    out[4 * (size_t)i] = 1.0 - a / std::sqrt(b * cc);
+    // the radius whose bins first hold 99 % of the atoms
+    double cum = 0.0, rr = g.nb * g.h;
+    for (int k = 0; k < g.nb; ++k) {
+      cum += h[(size_t)i * g.nb + k];
+      if (cum >= 0.99 * tot) {
+        rr = (k + 1) * g.h;
+        break;
+      }
+    }
+    R[(size_t)i] = rr;
+    out[4 * (size_t)i + 3] = rr;
+  }
+  CK(c, cudaMemcpyAsync(dR, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(c, launch_observables((int)c->es, p, g, ni, nullptr, sb, nullptr, dR, npts, dw, 1, c->st));
+  std::vector<double> w((size_t)ni * 2);
+  CK(c, cudaMemcpyAsync(w.data(), dw, w.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  bool finite = true;
+  for (int i = 0; i < ni; ++i) {
+    out[4 * (size_t)i + 1] = w[2 * (size_t)i];
+    out[4 * (size_t)i + 2] = w[2 * (size_t)i + 1];
+    for (int k = 0; k < 4; ++k) finite = finite && std::isfinite(out[4 * (size_t)i + k]);
+  }
+  return finite ? SPGPE_OK : fail(c, SPGPE_ENONFINITE, "non-finite observable");
+}
+
+}  // namespace
+
+extern "C" int spgpe_observables(spgpe_ctx *c, const void *psi, double *out) {
+  if (!c || !psi || !out) return fail(c, SPGPE_EINVAL, "NULL argument");
+  if (!c->cls.empty())
+    return for_classes(c, psi, false, [&](spgpe_ctx *k, void *p, int first) {
+      return spgpe_observables(k, p, out + 4 * (size_t)first);
+    });
+  void *p;
+  bool host;
+  int r = begin_psi(c, psi, &p, &host);
+  if (r) return r;
+  return observables_one(c, p, out);
+}
+
+extern "C" int spgpe_add_noise(spgpe_ctx *c, void *psi, double sigma, unsigned long long seed) {
+  if (!c || !psi) return fail(c, SPGPE_EINVAL, "NULL argument");
+  if (!(sigma >= 0) || !std::isfinite(sigma)) return fail(c, SPGPE_EINVAL, "sigma must be finite and >= 0");
+  auto one = [&](spgpe_ctx *k, void *p, int first) -> int {
+    const cudaError_t e = launch_add_noise((int)k->es, p, 2L * k->nx * k->ny, k->ninst, first, sigma, seed,
+                                           std::max(1, k->sms), k->st);
+    k->last_launches = 1;
+    return e == cudaSuccess ? SPGPE_OK : cuda_fail(k, e, "add_noise");
+  };
+  if (!c->cls.empty()) return for_classes(c, psi, true, one);
+  void *p;
+  bool host;
+  int r = begin_psi(c, psi, &p, &host);
+  if (r) return r;
+  if ((r = one(c, p, 0))) return r;
+  return end_psi(c, psi, host);
 }

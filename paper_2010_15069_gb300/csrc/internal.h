@@ -139,6 +139,24 @@ template <class T> cudaError_t launch_row_p(int flags, RowArgs a, cudaStream_t s
 template <class T> int colp_cols(int nx, int ny);
 template <class T> cudaError_t launch_col_p(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t s, int sms);
 template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t s);
+// Geometry of the Sec. 6 observables: grid, radial bin width h and count nb.
+struct ObsGeom {
+  int nx, ny, nb;
+  double xmax, ymax, dx, dy, h;
+};
+// phase 0: FP64 sums {rho_up rho_dn, rho_up^2, rho_dn^2, rho_up + rho_dn} per
+// block and instance into partials ([ninst][sum_blocks][4]) and the radial
+// histogram of the total density into hist ([ninst][nb], zeroed by the
+// caller); phase 1: winding numbers around radius R[inst] with npts points
+// into wind ([ninst][2]).  es = bytes per complex element.
+cudaError_t launch_observables(int es, const void *psi, const ObsGeom &g, int ninst, double *partials,
+                               int sum_blocks, double *hist, const double *R, int npts, double *wind, int phase,
+                               cudaStream_t st);
+// psi += sigma xi over ninst instances of n2 = 2 nx ny elements (global index
+// of the first: inst0), from the counter-based SplitMix64 stream `seed`.
+cudaError_t launch_add_noise(int es, void *psi, long n2, int ninst, long inst0, double sigma, unsigned long long seed,
+                             int sms, cudaStream_t st);
+
 // Round complex128 to complex64 (src_es 16, dst_es 8) or widen complex64 to
 // complex128 (8, 16): n complex values, grid of at most 8 blocks per SM.
 cudaError_t launch_convert(const void *src, int src_es, void *dst, int dst_es, long n, int sms, cudaStream_t s);

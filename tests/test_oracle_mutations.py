@@ -50,7 +50,19 @@ MUTANTS = {
     "energy_raman_half": [("eram += at(m->Omega, i) * std::real(std::conj(up[i]) * dn[i]);",
                            "eram += 0.5 * at(m->Omega, i) * std::real(std::conj(up[i]) * dn[i]);")],
     "energy_g12_half": [("+ m->g12 * ru * rd;\n  }", "+ 0.5 * m->g12 * ru * rd;\n  }")],
+    # Sec. 6 observables and annealing noise (pinned in test_oracle_observables.py)
+    "separation_no_sqrt": [("out[0] = 1.0 - a / std::sqrt(b * c);", "out[0] = 1.0 - a / (b * c);")],
+    "winding_clockwise": [("const double th = 2.0 * kPi * (double)(k % npts) / npts;",
+                           "const double th = -2.0 * kPi * (double)(k % npts) / npts;")],
+    "contour_90_percent": [("if (cum >= 0.99 * tot) {", "if (cum >= 0.9 * tot) {")],
+    "noise_variance_doubled": [("const double r = std::sqrt(-std::log(1.0 - u1));",
+                                "const double r = std::sqrt(-2.0 * std::log(1.0 - u1));")],
+    "splitmix_counter_from_zero": [("unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;",
+                                    "unsigned long long z = seed + c * 0x9E3779B97F4A7C15ull;")],
 }
+PIN_FILES = {name: "tests/test_oracle_observables.py" for name in
+             ("separation_no_sqrt", "winding_clockwise", "contour_90_percent", "noise_variance_doubled",
+              "splitmix_counter_from_zero")}
 
 
 @pytest.mark.slow
@@ -67,7 +79,7 @@ def test_pins_kill_mutant(tmp_path, name):
     for f in ("__init__.py", "_lib.py", "inputs.py"):
         shutil.copy(os.path.join(ROOT, "paper_2010_15069_gb300", f), tmp_path / "paper_2010_15069_gb300" / f)
     (tmp_path / "oracle" / "spgpe_oracle.cpp").write_text(src)
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+    r = subprocess.run([sys.executable, "-m", "pytest", PIN_FILES.get(name, "tests/test_oracle_pins.py"), "-x", "-q",
                         "-m", "not slow", "-p", "no:cacheprovider"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, f"mutant {name} survived:\n{r.stdout[-2000:]}"

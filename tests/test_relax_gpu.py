@@ -110,3 +110,27 @@ def test_batched_relaxation_freezes_each_instance_where_it_converged_alone(dtype
     for i in range(3):
         assert res[i] == alone[i][1]
         assert np.array_equal(got[i], alone[i][0]), i
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_relaxation_on_a_stream_replays_chunk_graphs_with_the_same_bits(dtype):
+    """On a stream of its own the relaxation captures one chunk in a CUDA graph
+    and replays it; on the legacy default stream (which cannot be captured) it
+    launches directly.  Both give the same bits and launch counts."""
+    p = small_problem()
+    npt = np.complex64 if dtype == "c64" else np.complex128
+    tol = 1e-8 if dtype == "c128" else 1e-4
+    psi0 = np.stack([inputs.vortex_spinor(p.grid, n_vortices=3 + i, radius=3.0, seed=70 + i)
+                     for i in range(2)]).astype(npt)
+    out = []
+    for stream in (None, torch.cuda.Stream()):
+        g = p.grid
+        with sp.Context(g.nx, g.ny, g.xmax, g.ymax, dtype, 2, stream=stream) as c:
+            c.set_potentials_separable(-1, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+            t = torch.from_numpy(psi0.copy()).cuda()
+            torch.cuda.synchronize()
+            res, steps = c.relax(t, DTAU, tol, 40000, check_every=100, ladder=True)
+            torch.cuda.synchronize()
+            out.append((t.cpu().numpy(), res, steps, c.last_launches()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2] and out[0][3] == out[1][3]
