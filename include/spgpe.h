@@ -230,6 +230,56 @@ int spgpe_sync(spgpe_ctx *ctx);
  * device psi only. */
 int spgpe_cufft_step_real(spgpe_ctx *ctx, void *psi, double dt, int nsteps);
 
+/* ---- Learned warm start: a Fourier neural operator (FNO) ----
+ * Not part of the paper's method: a network (the Fourier neural operator of
+ * Li et al., arXiv:2010.08895) trained on ground states this library computes,
+ * whose output seeds the imaginary-time relaxation of Sec. 3.2 (which stays
+ * the judge of the result: spgpe_relax).  It maps input fields
+ * a[batch][cin][n][n] to output fields out[batch][cout][n][n] (float32,
+ * device memory, x fastest):
+ *   v_0 = P a + p;  u_l = W_l v_l + w_l + S_l(v_l),  v_{l+1} = gelu(u_l)
+ *   (l < layers - 1), v_layers = u_{layers-1};  out = Q2 gelu(Q1 v + q1) + q2,
+ * gelu(x) = x Phi(x), and the spectral convolution S over the kept modes
+ * kx = 0..modes-1, ky = 0..modes-1 and n-modes..n-1:
+ *   vh = sum_{y,x} v exp(-2 pi i (kx x + ky y)/n);  oh[o] = sum_c R[ky][kx][o][c] vh[c];
+ *   S(v) = Re sum g_kx oh exp(+2 pi i (kx x + ky y)/n) / n^2,  g_0 = 1, g_kx = 2.
+ * Parameters are one float32 vector: P [width][cin], p [width]; per layer
+ * W_l [width][width], w_l [width], R_l [2 modes][modes][width][width][2]
+ * (real, imaginary); Q1 [hidden][width], q1 [hidden], Q2 [cout][hidden],
+ * q2 [cout].  The products use the weights rounded to bfloat16 and
+ * accumulate in float32; Adam updates the float32 masters.  The loss of a
+ * batch is the mean relative squared error
+ * sum_b ||out_b - target_b||^2 / ||target_b||^2 / batch.  n is a power of two
+ * with 2 modes <= n <= 4096.  A model is not thread-safe; calls are
+ * stream-ordered on cuda_stream and synchronise only where stated. */
+typedef struct spgpe_fno spgpe_fno;
+
+/* Allocate a model with seeded initial weights (matrices uniform in
+ * +-1/sqrt(fan_in), biases zero, spectral weights uniform in [0, 1)/width^2).
+ * EINVAL for non-positive or excessive sizes, ENOMEM/ECUDA on failure. */
+int spgpe_fno_create(spgpe_fno **out, int cin, int cout, int width, int modes, int layers, int hidden,
+                     unsigned long long seed, void *cuda_stream);
+/* Number of float32 parameters. */
+long spgpe_fno_num_params(const spgpe_fno *f);
+/* Copy the float32 master parameters to / from the host (synchronises); set
+ * also resets the Adam moments and step count. */
+int spgpe_fno_get_params(spgpe_fno *f, float *host);
+int spgpe_fno_set_params(spgpe_fno *f, const float *host);
+/* out = FNO(a) for a batch of inputs (device pointers). */
+int spgpe_fno_forward(spgpe_fno *f, const float *a, int batch, int n, float *out);
+/* Forward pass into out, loss (host, nullable; synchronises) and the gradient
+ * of the loss with respect to every parameter, copied to grad_host (host,
+ * nullable, num_params floats; synchronises). */
+int spgpe_fno_gradient(spgpe_fno *f, const float *a, const float *target, int batch, int n, float *out,
+                       double *loss, float *grad_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * batch with learning rate lr; out receives the forward pass and loss (host,
+ * nullable) the loss before the step. */
+int spgpe_fno_train_step(spgpe_fno *f, const float *a, const float *target, int batch, int n, float *out,
+                         double lr, double *loss);
+void spgpe_fno_destroy(spgpe_fno *f);
+const char *spgpe_fno_last_error(const spgpe_fno *f);
+
 void spgpe_destroy(spgpe_ctx *ctx);
 const char *spgpe_last_error(const spgpe_ctx *ctx);
 int spgpe_version(void);

@@ -26,7 +26,7 @@ from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_T
 __all__ = [
     "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SPGPE_RELAX_GIVE_UP",
     "SpgpeError",
-    "Context", "load",
+    "Context", "FNO", "load",
     "spgpe_init_grid", "spgpe_init_batch", "spgpe_init_multi", "spgpe_set_potentials", "spgpe_set_potentials_separable",
     "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_autotune", "spgpe_observables", "spgpe_add_noise", "spgpe_energy", "spgpe_norm", "spgpe_sync",
     "spgpe_cufft_step_real", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
@@ -184,6 +184,98 @@ def spgpe_timing(ctx):
     cnt = np.zeros(NKINDS, dtype=np.int32)
     check(load().spgpe_timing(ctx, _ptr(ms), _ptr(cnt)), ctx)
     return {KIND_NAMES[k]: (int(cnt[k]), float(ms[k])) for k in range(NKINDS) if cnt[k]}
+
+
+# ------------------------------------------------------------ learned warm start
+
+class FNO:
+    """The Fourier neural operator of the warm start (spgpe_fno_*): torch float32
+    CUDA tensors in and out, laid out [batch][channel][n][n]; parameters as a
+    numpy float32 vector in the layout documented in include/spgpe.h."""
+
+    def __init__(self, cin, cout, width=64, modes=32, layers=4, hidden=128, seed=0, stream=None):
+        self.cin, self.cout, self.width, self.modes, self.layers, self.hidden = cin, cout, width, modes, layers, hidden
+        s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        h = ctypes.c_void_p()
+        rc = load().spgpe_fno_create(ctypes.byref(h), int(cin), int(cout), int(width), int(modes), int(layers),
+                                     int(hidden), ctypes.c_ulonglong(int(seed) & (2 ** 64 - 1)), ctypes.c_void_p(s))
+        if rc != 0:
+            raise SpgpeError(rc, "spgpe_fno_create failed")
+        self._h = h.value
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = load().spgpe_fno_last_error(self._h)
+            raise SpgpeError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().spgpe_fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def num_params(self):
+        return int(load().spgpe_fno_num_params(self._h))
+
+    def get_params(self):
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        self._check(load().spgpe_fno_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        if theta.size != self.num_params():
+            raise ValueError("parameter vector of the wrong length")
+        self._check(load().spgpe_fno_set_params(self._h, theta.ctypes.data_as(ctypes.c_void_p)))
+
+    @staticmethod
+    def _dev(t, ch):
+        import torch  # device memory only
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.dim() != 4 or t.shape[1] != ch \
+                or t.shape[2] != t.shape[3]:
+            raise ValueError(f"expected a contiguous CUDA float32 tensor [batch][{ch}][n][n]")
+        return t.data_ptr()
+
+    def forward(self, a):
+        import torch
+        out = torch.empty((a.shape[0], self.cout, a.shape[2], a.shape[3]), dtype=torch.float32, device=a.device)
+        self._check(load().spgpe_fno_forward(self._h, ctypes.c_void_p(self._dev(a, self.cin)), int(a.shape[0]),
+                                             int(a.shape[2]), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def gradient(self, a, target):
+        """(loss, gradient as a numpy float32 vector, output tensor)."""
+        import torch
+        out = torch.empty_like(target)
+        g = np.zeros(self.num_params(), dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(load().spgpe_fno_gradient(self._h, ctypes.c_void_p(self._dev(a, self.cin)),
+                                              ctypes.c_void_p(self._dev(target, self.cout)), int(a.shape[0]),
+                                              int(a.shape[2]), ctypes.c_void_p(out.data_ptr()), ctypes.byref(loss),
+                                              g.ctypes.data_as(ctypes.c_void_p)))
+        return loss.value, g, out
+
+    def train_step(self, a, target, lr):
+        """One Adam step; returns the loss before it."""
+        import torch
+        out = torch.empty_like(target)
+        loss = ctypes.c_double()
+        self._check(load().spgpe_fno_train_step(self._h, ctypes.c_void_p(self._dev(a, self.cin)),
+                                                ctypes.c_void_p(self._dev(target, self.cout)), int(a.shape[0]),
+                                                int(a.shape[2]), ctypes.c_void_p(out.data_ptr()), float(lr),
+                                                ctypes.byref(loss)))
+        return loss.value
 
 
 # --------------------------------------------------------- convenience class

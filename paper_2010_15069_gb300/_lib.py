@@ -42,6 +42,15 @@ SIGNATURES = {
     "spgpe_relax": (_I, [_P, _P, _D, _D, _I, _I, _I, _P, _I, _D, _P, _P]),
     "spgpe_autotune": (_I, [_P, _P, _D, _P, _P]),
     "spgpe_observables": (_I, [_P, _P, _P]),
+    "spgpe_fno_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _I, ctypes.c_ulonglong, _P]),
+    "spgpe_fno_num_params": (ctypes.c_long, [_P]),
+    "spgpe_fno_get_params": (_I, [_P, _P]),
+    "spgpe_fno_set_params": (_I, [_P, _P]),
+    "spgpe_fno_forward": (_I, [_P, _P, _I, _I, _P]),
+    "spgpe_fno_gradient": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "spgpe_fno_train_step": (_I, [_P, _P, _P, _I, _I, _P, _D, _P]),
+    "spgpe_fno_destroy": (None, [_P]),
+    "spgpe_fno_last_error": (ctypes.c_char_p, [_P]),
     "spgpe_add_noise": (_I, [_P, _P, _D, ctypes.c_ulonglong]),
 }
 NKINDS = 9
