@@ -322,8 +322,13 @@ def run_fused(args):
     with torch.cuda.stream(stream):
         c, t, _ = make_workload(B, dtype, stream=stream)
     pts = B * NX * NY
-    # the library's autotuner picks the pass variants for this batch (scratch copy; psi unchanged)
-    choice, tune_ms = c.autotune(t, DT)
+    if args.schedule == "auto":
+        # the library's autotuner picks the pass variants for this batch (scratch copy; psi unchanged)
+        choice, tune_ms = c.autotune(t, DT)
+    else:
+        # a fixed schedule (e.g. for a profiler run, under which the tuner's timings mean nothing);
+        # set through the environment variable the context reads when it is created
+        choice, tune_ms = np.array([3 if args.schedule == "persistent" else 0]), None
 
     def barrier():
         if dist is not None:
@@ -394,7 +399,8 @@ def run_fused(args):
         "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
         "config": dict(workload_config(B, dtype),
                        schedule={"persistent_row": bool(choice[0] & 1), "persistent_col": bool(choice[0] & 2),
-                                 "autotune_ms_per_step": float(tune_ms[0])}),
+                                 "chosen_by": args.schedule,
+                                 "autotune_ms_per_step": float(tune_ms[0]) if tune_ms is not None else None}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
@@ -422,6 +428,8 @@ def main():
     ap.add_argument("--impl", choices=["fused", "reference"], default="fused")
     ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES)
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--schedule", choices=["auto", "persistent", "plain"], default="auto",
+                    help="pass variants: autotuned (default) or fixed")
     ap.add_argument("--ttr-instances", type=int, default=8,
                     help="sweep instances of the time-to-residual comparison (0: skip it)")
     args = ap.parse_args()
@@ -432,6 +440,8 @@ def main():
     else:
         from paper_2010_15069_gb300 import build
         build.build()
+        if args.schedule != "auto":
+            os.environ["SPGPE_PERSISTENT"] = "2" if args.schedule == "persistent" else "0"
         run_fused(args)
 
 

@@ -262,6 +262,7 @@ template <int K> __device__ __forceinline__ void block_sum(double (&v)[K]) {
 // stages synchronise with a warp barrier over `mask` instead of the block.
 template <class T, bool WARP_LOCAL = false> struct RowAcc {
   static constexpr int SH = pad_shift(sizeof(cx<T>));
+  static constexpr bool kWarpLocal = WARP_LOCAL;
   cx<T> *base;
   int stride;
   unsigned mask;
@@ -310,51 +311,88 @@ template <class T, int C> struct ColAccC {
 // doubled X (exact: the two factors are the same rotation about sigma_x).
 // TIER: the phase tier of opD, one instantiation per tier so that each warp
 // runs straight-line code.
+// R_end and/or R_start at one point x of row y (both components).
+template <class T, int N, int F, int TIER>
+__device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4<T> *tab, const q4<T> &ty,
+                                      const q4<T> *p2, T g11, T g22, T g12, T htau, T xang, int pieces, bool ymerge,
+                                      T tm, T sm, double (&nsum)[2]) {
+  constexpr bool IMAG = (F & F_IMAG) != 0;
+  constexpr bool MERGE = !IMAG && (F & F_REND) && (F & F_RSTART) && !(F & F_PART);
+  const q4<T> px = tab[x];
+  T vu = px.x + ty.x, vd = px.y + ty.y;
+  T q2z = T(0);
+  if (p2) {
+    const q4<T> q = p2[(long)y * N + x];
+    vu += q.x;
+    vd += q.y;
+    q2z = q.z;
+  }
+  const XPoint<T> xc = xpoint<IMAG, T>(px, ty, p2 != nullptr, q2z, xang);
+  if constexpr (MERGE) {
+    applyX<false>(u, d, xc, pieces);
+    opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+    applyX2(u, d, xc, pieces, ymerge, tm, sm);
+    opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+    applyX<false>(u, d, xc, pieces);
+  } else {
+    if constexpr (F & F_REND) {
+      applyX<IMAG>(u, d, xc, pieces);
+      opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+      applyX<IMAG>(u, d, xc, pieces);
+    }
+    if constexpr (F & F_PART) {
+      nsum[0] += double(cabs2(u));
+      nsum[1] += double(cabs2(d));
+    }
+    if constexpr (F & F_RSTART) {
+      applyX<IMAG>(u, d, xc, pieces);
+      opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+      applyX<IMAG>(u, d, xc, pieces);
+    }
+  }
+}
+
+// R_end and/or R_start at this thread's H points (both components).
+// MERGE (the fused real-time pass): X D X X D X with the middle X X as one
+// doubled X (exact: the two factors are the same rotation about sigma_x).
+// TIER: the phase tier of opD, one instantiation per tier so that each warp
+// runs straight-line code.
 template <class T, int LOGN, int LOGE, int F, int TIER>
 __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&pd)[(1 << LOGE) / 2], int t, int comp,
                                          int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T g11, T g22,
                                          T g12, T htau, T xang, int pieces, bool ymerge, T tm, T sm,
                                          double (&nsum)[2]) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
-  constexpr bool IMAG = (F & F_IMAG) != 0;
-  constexpr bool MERGE = !IMAG && (F & F_REND) && (F & F_RSTART) && !(F & F_PART);
 #pragma unroll
+  for (int j = 0; j < H; ++j)
+    r_one<T, N, F, TIER>(pu[j], pd[j], t + (j + comp * H) * TT, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces,
+                         ymerge, tm, sm, nsum);
+}
+
+// The same points with both components met in shared memory instead of
+// registers (up: the row's component-up area, dn: component down; position p
+// at index p + (p >> SH)): a short loop instead of H unrolled points keeps
+// the row pass's code small.
+#ifndef SPGPE_ROW_R_SMEM
+#define SPGPE_ROW_R_SMEM 0
+#endif
+#ifndef SPGPE_ROW_R_UNROLL
+#define SPGPE_ROW_R_UNROLL 2
+#endif
+template <class T, int LOGN, int LOGE, int F, int TIER>
+__device__ __forceinline__ void r_points_smem(cx<T> *up, cx<T> *dn, int t, int comp, int y, const q4<T> *tab,
+                                              const q4<T> &ty, const q4<T> *p2, T g11, T g22, T g12, T htau, T xang,
+                                              int pieces, bool ymerge, T tm, T sm, double (&nsum)[2]) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
+  constexpr int SH = pad_shift(sizeof(cx<T>));
+  constexpr int RU = SPGPE_ROW_R_UNROLL;
+#pragma unroll RU
   for (int j = 0; j < H; ++j) {
-    const int x = t + (j + comp * H) * TT;
-    cx<T> &u = pu[j];
-    cx<T> &d = pd[j];
-    const q4<T> px = tab[x];
-    T vu = px.x + ty.x, vd = px.y + ty.y;
-    T q2z = T(0);
-    if (p2) {
-      const q4<T> q = p2[(long)y * N + x];
-      vu += q.x;
-      vd += q.y;
-      q2z = q.z;
-    }
-    const XPoint<T> xc = xpoint<IMAG, T>(px, ty, p2 != nullptr, q2z, xang);
-    if constexpr (MERGE) {
-      applyX<false>(u, d, xc, pieces);
-      opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
-      applyX2(u, d, xc, pieces, ymerge, tm, sm);
-      opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
-      applyX<false>(u, d, xc, pieces);
-    } else {
-      if constexpr (F & F_REND) {
-        applyX<IMAG>(u, d, xc, pieces);
-        opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
-        applyX<IMAG>(u, d, xc, pieces);
-      }
-      if constexpr (F & F_PART) {
-        nsum[0] += double(cabs2(u));
-        nsum[1] += double(cabs2(d));
-      }
-      if constexpr (F & F_RSTART) {
-        applyX<IMAG>(u, d, xc, pieces);
-        opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
-        applyX<IMAG>(u, d, xc, pieces);
-      }
-    }
+    const int x = t + (j + comp * H) * TT, ix = x + (x >> SH);
+    cx<T> u = up[ix], d = dn[ix];
+    r_one<T, N, F, TIER>(u, d, x, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum);
+    up[ix] = u;
+    dn[ix] = d;
   }
 }
 
@@ -375,15 +413,6 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     for (int m = 0; m < E; ++m) v[0][m] = cscale(v[0][m], sc);
   }
   if constexpr (F & (F_REND | F_RSTART)) {
-    // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
-    cx<T> pu[H], pd[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const cx<T> snd = comp ? v[0][j] : v[0][H + j];
-      const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
-      pu[j] = comp ? rcv : v[0][j];
-      pd[j] = comp ? v[0][H + j] : rcv;
-    }
     const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
     const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
     const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
@@ -391,42 +420,86 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     T htau, xang;
     if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
     const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
+    const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
+    T tm = T(0), sm = T(0);
+    bool ymerge = false;
+    if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
     // One phase tier per warp: the shortest series whose range holds |htau e|
     // at every point of the warp.  e <= Vb + G rho_tot with Vb = max |V +-
     // delta/2| of the instance and G = max(|g11|, |g22|) + |g12|; rho_tot =
     // |u|^2 + |d|^2 at a point is left unchanged by real-time R (5 % margin
     // for the imaginary-time X).
-    T rmax = T(0);
+    constexpr bool SMEM_R = SPGPE_ROW_R_SMEM && Acc::kWarpLocal;
+    if constexpr (SMEM_R) {
+      // rho_tot <= max |own|^2 + max |partner's|^2 over the thread's positions
+      T own = T(0);
 #pragma unroll
-    for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
-                                                      d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
-    const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
-    const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
-    const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
-    const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
-    T tm = T(0), sm = T(0);
-    bool ymerge = false;
-    if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
+      for (int m = 0; m < E; ++m) own = fmax(own, d_fma(v[0][m].re, v[0][m].re, v[0][m].im * v[0][m].im));
+      const T rmax = own + __shfl_xor_sync(mask, own, half);
+      const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
+      const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
+      const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
+      constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
+      cx<T> *up = acc.base - comp * PADN, *dn = up + PADN;
+      acc.sync();  // the transform's last exchange has been read
+#pragma unroll
+      for (int m = 0; m < E; ++m) acc.st(0, t + m * TT, v[0][m]);
+      acc.sync();
+#define SPGPE_R_POINTS(TIER) \
+  r_points_smem<T, LOGN, LOGE, F, TIER>(up, dn, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum)
+      if constexpr (sizeof(T) == 8) {
+        SPGPE_R_POINTS(2);
+      } else {
+        if (!IMAG && tiny)
+          SPGPE_R_POINTS(0);
+        else if (small)
+          SPGPE_R_POINTS(1);
+        else
+          SPGPE_R_POINTS(2);
+      }
+#undef SPGPE_R_POINTS
+      acc.sync();
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[0][m] = acc.ld(0, t + m * TT);
+      acc.sync();  // the next transform's first exchange overwrites the area
+    } else {
+      // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
+      cx<T> pu[H], pd[H];
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const cx<T> snd = comp ? v[0][j] : v[0][H + j];
+        const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
+        pu[j] = comp ? rcv : v[0][j];
+        pd[j] = comp ? v[0][H + j] : rcv;
+      }
+      T rmax = T(0);
+#pragma unroll
+      for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
+                                                        d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
+      const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
+      const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
+      const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
 #define SPGPE_R_POINTS(TIER) \
   r_points<T, LOGN, LOGE, F, TIER>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum)
-    if constexpr (sizeof(T) == 8) {
-      SPGPE_R_POINTS(2);
-    } else {
-      if (!IMAG && tiny)  // imaginary time has no tier 0
-        SPGPE_R_POINTS(0);
-      else if (small)
-        SPGPE_R_POINTS(1);
-      else
+      if constexpr (sizeof(T) == 8) {
         SPGPE_R_POINTS(2);
-    }
+      } else {
+        if (!IMAG && tiny)  // imaginary time has no tier 0
+          SPGPE_R_POINTS(0);
+        else if (small)
+          SPGPE_R_POINTS(1);
+        else
+          SPGPE_R_POINTS(2);
+      }
 #undef SPGPE_R_POINTS
-    // scatter back to one component per thread
+      // scatter back to one component per thread
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const cx<T> snd = comp ? pu[j] : pd[j];
-      const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
-      v[0][j] = comp ? rcv : pu[j];
-      v[0][H + j] = comp ? pd[j] : rcv;
+      for (int j = 0; j < H; ++j) {
+        const cx<T> snd = comp ? pu[j] : pd[j];
+        const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
+        v[0][j] = comp ? rcv : pu[j];
+        v[0][H + j] = comp ? pd[j] : rcv;
+      }
     }
   }
   if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 1>(v, t, a.tw, acc);
