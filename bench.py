@@ -208,6 +208,116 @@ def time_to_residual(B):
                           "max_abs_dpsi": float(np.abs(lad[both] - np.stack(plain)[both]).max()) if both else None}}
 
 
+# ------------------------------------------------------- uneven sweep batch
+
+SWEEP_CLASSES = [(256, 64), (512, 16), (1024, 4)]   # (grid, instances): 12.58 M points per component
+SWEEP_BOX, SWEEP_DTAU = 12.0, 5e-3
+
+
+def sweep_throughput(steps=40):
+    """Imaginary-time steps of the uneven sweep batch (64 x 256^2 + 16 x 512^2 +
+    4 x 1024^2, complex64, box [-12, 12]^2, kL = 1, per-instance g, g12, Omega,
+    detuning gradient from the sweep generator) as one multi-size batch (size
+    classes side by side on their own streams) and as three same-size contexts
+    run one after another; grid-point-steps/s of each."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    total = sum(k for _, k in SWEEP_CLASSES)
+    prm = inputs.sweep_params(total, seed=3)
+    classes = [(n, n, k, SWEEP_BOX, SWEEP_BOX) for n, k in SWEEP_CLASSES]
+    probs, i = [], 0
+    for n, k in SWEEP_CLASSES:
+        for _ in range(k):
+            q = prm[i]
+            probs.append(inputs.problem(n, n, SWEEP_BOX, SWEEP_BOX, Omega=q["Omega"], delta_slope=q["delta_slope"],
+                                        g11=q["g"], g22=q["g"], g12=q["g12"], kL=1.0))
+            i += 1
+    psi = [inputs.gaussian_spinor(p.grid, width=3.0, seed=40 + j).astype(np.complex64) for j, p in enumerate(probs)]
+    pts = sum(n * n * k for n, k in SWEEP_CLASSES)
+    stream = torch.cuda.Stream()
+
+    def timed(run):
+        run(3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e-3
+
+    with sp.Context.multi(classes, "c64", stream=stream) as c:
+        for j, p in enumerate(probs):
+            c.set_potentials_separable(j, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+        flat = torch.from_numpy(np.concatenate([x.ravel() for x in psi])).cuda()
+        c.autotune(flat, 5e-4)
+        t_multi = timed(lambda k: c.step_imag(flat, SWEEP_DTAU, k))
+    ctxs, bufs, j = [], [], 0
+    for n, k in SWEEP_CLASSES:
+        cc = sp.Context(n, n, SWEEP_BOX, SWEEP_BOX, "c64", ninst=k, stream=stream)
+        for q in range(k):
+            p = probs[j + q]
+            cc.set_potentials_separable(q, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+        buf = torch.from_numpy(np.stack(psi[j:j + k])).cuda()
+        cc.autotune(buf, 5e-4)
+        ctxs.append(cc)
+        bufs.append(buf)
+        j += k
+    t_seq = timed(lambda k: [cc.step_imag(b, SWEEP_DTAU, k) for cc, b in zip(ctxs, bufs)])
+    for cc in ctxs:
+        cc.close()
+    return {"workload": "64 x 256^2 + 16 x 512^2 + 4 x 1024^2 instances (12.58 M points per component), c64, "
+                        f"imaginary time dtau={SWEEP_DTAU:g}, {steps} steps, sweep parameters (seed 3)",
+            "multi_size_batch_pt_steps_per_s": pts * steps / t_multi,
+            "same_size_contexts_in_turn_pt_steps_per_s": pts * steps / t_seq,
+            "ratio": t_seq / t_multi}
+
+
+# ------------------------------------------------------- warm-start network
+
+def fno_flops(n, cin=6, cout=4, W=64, M=32, L=4, H=128):
+    """Multiply-add count x 2 of one forward pass of the warm-start FNO on n x n
+    (the contractions as the kernels run them: the truncated DFTs as products
+    with twiddle matrices, complex products counted as 4 real)."""
+    P = n * n
+    lift = 2 * P * W * cin
+    layer = (2 * W * n * n * 2 * M          # along x (real x interleaved complex)
+             + 8 * 2 * M * M * n * W         # along y (complex)
+             + 8 * W * W * 2 * M * M         # per-mode channel mixing
+             + 8 * n * M * 2 * M * W         # inverse along y
+             + 2 * W * n * 2 * M * n         # real part of the inverse along x
+             + 2 * P * W * W)                # pointwise W_l
+    proj = 2 * P * W * H + 2 * P * H * cout
+    return lift + L * layer + proj
+
+
+def fno_throughput(n=256, batch=4, steps=10):
+    """Training steps (forward, backward, Adam) of the warm-start FNO at its full
+    size (width 64, 32 modes, 4 layers, 67.1 M parameters) on n x n inputs:
+    samples/s and the achieved FP32 rate (training = 3 forward passes) against
+    the FP32 FMA peak of the CUDA cores at the sampled clock."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    rng = np.random.default_rng(0)
+    a = torch.from_numpy(rng.standard_normal((batch, 6, n, n)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.standard_normal((batch, 4, n, n)).astype(np.float32)).cuda()
+    with sp.FNO(6, 4, width=64, modes=32, layers=4, hidden=128, seed=0) as f:
+        f.train_step(a, y, 1e-4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            f.train_step(a, y, 1e-4)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3 / steps
+    flop = 3 * fno_flops(n) * batch
+    return {"workload": f"FNO width 64, 32 modes, 4 layers, hidden 128 (67.1 M parameters), {n}x{n}, batch {batch}, "
+                        "bfloat16 weights, FP32 accumulate, one Adam step per batch",
+            "ms_per_train_step": sec * 1e3, "samples_per_s": batch / sec,
+            "achieved_tflops": flop / sec / 1e12, "bound": "alu"}
+
+
 # ------------------------------------------------------------- CPU oracle
 
 def oracle_rate(budget_s=12.0, max_steps=400):
@@ -257,6 +367,11 @@ def measured_traffic(key):
             if len(parts) == 3 and parts[0] == "traffic_bytes_per_launch" and parts[1] == key:
                 return int(parts[2])
     return None
+
+
+def torch_sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def peaks():
@@ -415,6 +530,16 @@ def run_fused(args):
     }
     if world == 1 and args.ttr_instances > 0:
         line["time_to_residual"] = time_to_residual(args.ttr_instances)
+    if world == 1 and args.sweep:
+        line["uneven_sweep"] = sweep_throughput()
+    if world == 1 and args.fno:
+        fn = fno_throughput()
+        sm = line["clocks"].get("sm_mhz") or 2070.0
+        # FP32 FMA peak of the CUDA cores: SMs x 128 lanes x 2 flop x clock
+        peak = torch_sm_count() * 128 * 2 * sm * 1e6 / 1e12
+        fn.update(peak_tflops=peak, frac=fn["achieved_tflops"] / peak,
+                  peak_source="derived: SMs x 128 FP32 lanes x 2 x sampled SM clock")
+        line["warm_start_fno"] = fn
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -430,6 +555,8 @@ def main():
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--schedule", choices=["auto", "persistent", "plain"], default="auto",
                     help="pass variants: autotuned (default) or fixed")
+    ap.add_argument("--sweep", type=int, default=1, help="1: also time the uneven sweep batch (0: skip)")
+    ap.add_argument("--fno", type=int, default=1, help="1: also time training of the warm-start FNO (0: skip)")
     ap.add_argument("--ttr-instances", type=int, default=8,
                     help="sweep instances of the time-to-residual comparison (0: skip it)")
     args = ap.parse_args()

@@ -262,7 +262,6 @@ template <int K> __device__ __forceinline__ void block_sum(double (&v)[K]) {
 // stages synchronise with a warp barrier over `mask` instead of the block.
 template <class T, bool WARP_LOCAL = false> struct RowAcc {
   static constexpr int SH = pad_shift(sizeof(cx<T>));
-  static constexpr bool kWarpLocal = WARP_LOCAL;
   cx<T> *base;
   int stride;
   unsigned mask;
@@ -369,33 +368,6 @@ __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&p
                          ymerge, tm, sm, nsum);
 }
 
-// The same points with both components met in shared memory instead of
-// registers (up: the row's component-up area, dn: component down; position p
-// at index p + (p >> SH)): a short loop instead of H unrolled points keeps
-// the row pass's code small.
-#ifndef SPGPE_ROW_R_SMEM
-#define SPGPE_ROW_R_SMEM 0
-#endif
-#ifndef SPGPE_ROW_R_UNROLL
-#define SPGPE_ROW_R_UNROLL 2
-#endif
-template <class T, int LOGN, int LOGE, int F, int TIER>
-__device__ __forceinline__ void r_points_smem(cx<T> *up, cx<T> *dn, int t, int comp, int y, const q4<T> *tab,
-                                              const q4<T> &ty, const q4<T> *p2, T g11, T g22, T g12, T htau, T xang,
-                                              int pieces, bool ymerge, T tm, T sm, double (&nsum)[2]) {
-  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
-  constexpr int SH = pad_shift(sizeof(cx<T>));
-  constexpr int RU = SPGPE_ROW_R_UNROLL;
-#pragma unroll RU
-  for (int j = 0; j < H; ++j) {
-    const int x = t + (j + comp * H) * TT, ix = x + (x >> SH);
-    cx<T> u = up[ix], d = dn[ix];
-    r_one<T, N, F, TIER>(u, d, x, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum);
-    up[ix] = u;
-    dn[ix] = d;
-  }
-}
-
 // Row-pass compute on registers already loaded: v holds this thread's
 // component at positions t + m*TT of row y.  tab points at the instance's
 // x step table (global or shared memory).  Returns the FP64 atom-number
@@ -429,77 +401,42 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     // delta/2| of the instance and G = max(|g11|, |g22|) + |g12|; rho_tot =
     // |u|^2 + |d|^2 at a point is left unchanged by real-time R (5 % margin
     // for the imaginary-time X).
-    constexpr bool SMEM_R = SPGPE_ROW_R_SMEM && Acc::kWarpLocal;
-    if constexpr (SMEM_R) {
-      // rho_tot <= max |own|^2 + max |partner's|^2 over the thread's positions
-      T own = T(0);
+    // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
+    cx<T> pu[H], pd[H];
 #pragma unroll
-      for (int m = 0; m < E; ++m) own = fmax(own, d_fma(v[0][m].re, v[0][m].re, v[0][m].im * v[0][m].im));
-      const T rmax = own + __shfl_xor_sync(mask, own, half);
-      const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
-      const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
-      const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
-      constexpr int PADN = row_pad_n(N, sizeof(cx<T>));
-      cx<T> *up = acc.base - comp * PADN, *dn = up + PADN;
-      acc.sync();  // the transform's last exchange has been read
+    for (int j = 0; j < H; ++j) {
+      const cx<T> snd = comp ? v[0][j] : v[0][H + j];
+      const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
+      pu[j] = comp ? rcv : v[0][j];
+      pd[j] = comp ? v[0][H + j] : rcv;
+    }
+    T rmax = T(0);
 #pragma unroll
-      for (int m = 0; m < E; ++m) acc.st(0, t + m * TT, v[0][m]);
-      acc.sync();
-#define SPGPE_R_POINTS(TIER) \
-  r_points_smem<T, LOGN, LOGE, F, TIER>(up, dn, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum)
-      if constexpr (sizeof(T) == 8) {
-        SPGPE_R_POINTS(2);
-      } else {
-        if (!IMAG && tiny)
-          SPGPE_R_POINTS(0);
-        else if (small)
-          SPGPE_R_POINTS(1);
-        else
-          SPGPE_R_POINTS(2);
-      }
-#undef SPGPE_R_POINTS
-      acc.sync();
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[0][m] = acc.ld(0, t + m * TT);
-      acc.sync();  // the next transform's first exchange overwrites the area
-    } else {
-      // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
-      cx<T> pu[H], pd[H];
-#pragma unroll
-      for (int j = 0; j < H; ++j) {
-        const cx<T> snd = comp ? v[0][j] : v[0][H + j];
-        const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
-        pu[j] = comp ? rcv : v[0][j];
-        pd[j] = comp ? v[0][H + j] : rcv;
-      }
-      T rmax = T(0);
-#pragma unroll
-      for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
-                                                        d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
-      const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
-      const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
-      const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
+    for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
+                                                      d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
+    const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
+    const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
+    const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
 #define SPGPE_R_POINTS(TIER) \
   r_points<T, LOGN, LOGE, F, TIER>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum)
-      if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(T) == 8) {
+      SPGPE_R_POINTS(2);
+    } else {
+      if (!IMAG && tiny)  // imaginary time has no tier 0
+        SPGPE_R_POINTS(0);
+      else if (small)
+        SPGPE_R_POINTS(1);
+      else
         SPGPE_R_POINTS(2);
-      } else {
-        if (!IMAG && tiny)  // imaginary time has no tier 0
-          SPGPE_R_POINTS(0);
-        else if (small)
-          SPGPE_R_POINTS(1);
-        else
-          SPGPE_R_POINTS(2);
-      }
+    }
 #undef SPGPE_R_POINTS
-      // scatter back to one component per thread
+    // scatter back to one component per thread
 #pragma unroll
-      for (int j = 0; j < H; ++j) {
-        const cx<T> snd = comp ? pu[j] : pd[j];
-        const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
-        v[0][j] = comp ? rcv : pu[j];
-        v[0][H + j] = comp ? pd[j] : rcv;
-      }
+    for (int j = 0; j < H; ++j) {
+      const cx<T> snd = comp ? pu[j] : pd[j];
+      const cx<T> rcv = {__shfl_xor_sync(mask, snd.re, half), __shfl_xor_sync(mask, snd.im, half)};
+      v[0][j] = comp ? rcv : pu[j];
+      v[0][H + j] = comp ? pd[j] : rcv;
     }
   }
   if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 1>(v, t, a.tw, acc);
