@@ -443,7 +443,7 @@ def run_fused(args):
     else:
         # a fixed schedule (e.g. for a profiler run, under which the tuner's timings mean nothing);
         # set through the environment variable the context reads when it is created
-        choice, tune_ms = np.array([3 if args.schedule == "persistent" else 0]), None
+        choice, tune_ms = np.array([{"persistent": 3, "warp": 5, "plain": 0}[args.schedule]]), None
 
     def barrier():
         if dist is not None:
@@ -513,7 +513,8 @@ def run_fused(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
         "config": dict(workload_config(B, dtype),
-                       schedule={"persistent_row": bool(choice[0] & 1), "persistent_col": bool(choice[0] & 2),
+                       schedule={"persistent_row": bool(choice[0] & 1),
+                                 "column_pass": ["plain", "persistent TMA", "warp-local TMA"][int(choice[0]) >> 1],
                                  "chosen_by": args.schedule,
                                  "autotune_ms_per_step": float(tune_ms[0]) if tune_ms is not None else None}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -553,7 +554,7 @@ def main():
     ap.add_argument("--impl", choices=["fused", "reference"], default="fused")
     ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES)
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
-    ap.add_argument("--schedule", choices=["auto", "persistent", "plain"], default="auto",
+    ap.add_argument("--schedule", choices=["auto", "persistent", "warp", "plain"], default="auto",
                     help="pass variants: autotuned (default) or fixed")
     ap.add_argument("--sweep", type=int, default=1, help="1: also time the uneven sweep batch (0: skip)")
     ap.add_argument("--fno", type=int, default=1, help="1: also time training of the warm-start FNO (0: skip)")
@@ -568,7 +569,9 @@ def main():
         from paper_2010_15069_gb300 import build
         build.build()
         if args.schedule != "auto":
-            os.environ["SPGPE_PERSISTENT"] = "2" if args.schedule == "persistent" else "0"
+            os.environ["SPGPE_PERSISTENT"] = "0" if args.schedule == "plain" else "2"
+            if args.schedule != "plain":
+                os.environ["SPGPE_COLPASS"] = "warp" if args.schedule == "warp" else "tma"
         run_fused(args)
 
 

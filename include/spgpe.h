@@ -171,14 +171,16 @@ int spgpe_relax(spgpe_ctx *ctx, void *psi, double dtau, double tol, int max_step
 
 /* Autotuning of the pass schedule: for the grid of a single-size context, or
  * for every size class of a multi-size batch, time real-time steps S(dt) of
- * each of the four variants (bit 0 of the variant: persistent row pass, in
- * which each warp or block streams its next rows into shared memory while it
- * transforms the current ones, else one row group per block; bit 1:
- * persistent TMA column pass, else one column tile per block) on a scratch
- * copy of psi (psi itself is not changed), and keep the fastest for all later
- * calls (complex64 twins included).  choice_out (host, nullable): the chosen
- * variant per class (one entry for a single-size context); ms_out (host,
- * nullable): its time per step in milliseconds.  Synchronises. */
+ * each schedule (variant v: bit 0 set = persistent row pass, in which each
+ * warp or block streams its next rows into shared memory while it transforms
+ * the current ones, else one row group per block; v >> 1 = column pass:
+ * 0 one column tile per block, 1 persistent TMA pass, 2 warp-local TMA pass
+ * with the 128-byte swizzle (complex64 grids with ny = 256 only)) on a
+ * scratch copy of psi (psi itself is not changed), twice each, and keep the
+ * fastest for all later calls (complex64 twins included).  choice_out (host,
+ * nullable): the chosen variant per class (one entry for a single-size
+ * context); ms_out (host, nullable): its time per step in milliseconds.
+ * Synchronises. */
 int spgpe_autotune(spgpe_ctx *ctx, const void *psi, double dt, int *choice_out, double *ms_out);
 
 /* Energy functional whose variation is H Psi, per instance:

@@ -81,8 +81,9 @@ struct spgpe_ctx {
   int sms = 0;
   bool persistent_row = true;
   bool persistent_col = true;
-  const void *map_psi = nullptr;
-  CUtensorMap map{};
+  bool warp_col = true;  // the warp-local column pass where it applies (ny = 256, complex64)
+  const void *map_psi = nullptr, *map_sw_psi = nullptr;
+  CUtensorMap map{}, map_sw{};
   void *d_gparT = nullptr;
 
   // Batch over several grid sizes: the size classes are child contexts, each
@@ -466,11 +467,11 @@ cudaError_t row(spgpe_ctx *c, int flags, const RowArgs &a) {
   });
 }
 
-// Tensor map over the spinor buffer viewed as [ninst*2*ny rows][nx complex]
-// (8-byte elements: one complex64, or half a complex128), with a box of C
-// complex columns by min(ny, 256) rows.
-cudaError_t ensure_map(spgpe_ctx *c, const void *psi) {
-  if (c->map_psi == psi) return cudaSuccess;
+// Tensor maps over the spinor buffer viewed as [ninst*2*ny rows][nx complex]
+// (8-byte elements: one complex64, or half a complex128): `map` with boxes
+// of C complex columns by min(ny, 256) rows for the persistent column pass,
+// `map_sw` with 16 x 256 boxes and the 128-byte swizzle for the warp-local one.
+cudaError_t encode_map(spgpe_ctx *c, const void *psi, CUtensorMap *m, int cols, bool swizzle) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -480,24 +481,45 @@ cudaError_t ensure_map(spgpe_ctx *c, const void *psi) {
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const int xm = c->dtype == SPGPE_C64 ? 1 : 2;
-  const int C = c->dtype == SPGPE_C64 ? colp_cols<float>(c->nx, c->ny) : colp_cols<double>(c->nx, c->ny);
   const cuuint64_t dims[2] = {(cuuint64_t)c->nx * xm, (cuuint64_t)c->ninst * 2 * c->ny};
   const cuuint64_t strides[1] = {(cuuint64_t)c->nx * c->es};
-  const cuuint32_t box[2] = {(cuuint32_t)(C * xm), (cuuint32_t)std::min(c->ny, 256)};
+  const cuuint32_t box[2] = {(cuuint32_t)(cols * xm), (cuuint32_t)std::min(c->ny, 256)};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(&c->map, c->dtype == SPGPE_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                            2, const_cast<void *>(psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  c->map_psi = psi;
-  return cudaSuccess;
+  const CUresult r = encode(m, c->dtype == SPGPE_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                            const_cast<void *>(psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t ensure_map(spgpe_ctx *c, const void *psi) {
+  if (c->map_psi == psi) return cudaSuccess;
+  const int C = c->dtype == SPGPE_C64 ? colp_cols<float>(c->nx, c->ny) : colp_cols<double>(c->nx, c->ny);
+  const cudaError_t e = encode_map(c, psi, &c->map, C, false);
+  if (e == cudaSuccess) c->map_psi = psi;
+  return e;
+}
+
+cudaError_t ensure_map_sw(spgpe_ctx *c, const void *psi) {
+  if (c->map_sw_psi == psi) return cudaSuccess;
+  const cudaError_t e = encode_map(c, psi, &c->map_sw, 16, true);
+  if (e == cudaSuccess) c->map_sw_psi = psi;
+  return e;
+}
+
+bool warp_col_applies(const spgpe_ctx *c) { return c->dtype == SPGPE_C64 && c->ny == 256 && c->nx >= 16; }
+
 cudaError_t col(spgpe_ctx *c, bool imag, const ColArgs &a) {
-  bool p = c->persistent_col && c->sms > 0 && aligned16(a.psi);
+  const bool ok16 = c->sms > 0 && aligned16(a.psi);
+  bool w = c->warp_col && ok16 && warp_col_applies(c);
+  if (w && ensure_map_sw(c, a.psi) != cudaSuccess) w = false;
+  bool p = !w && c->persistent_col && ok16;
   if (p && ensure_map(c, a.psi) != cudaSuccess) p = false;
   return timed(c, imag ? 8 : 3, [&] {
+    if (w) {
+      const cudaError_t e = launch_col_w<float>(imag, a, c->map_sw, c->st, c->sms);
+      if (e != cudaErrorNotSupported) return e;
+    }
     if (p) {
       const cudaError_t e = c->dtype == SPGPE_C64 ? launch_col_p<float>(imag, a, c->map, c->st, c->sms)
                                                   : launch_col_p<double>(imag, a, c->map, c->st, c->sms);
@@ -609,12 +631,19 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
       c->sms = 0;
     cudaGetLastError();
     // SPGPE_PERSISTENT selects the pass variants: 0 plain passes, 1 persistent
-    // column pass only, 2 persistent row and column passes (default).
+    // column passes only, 2 persistent row and column passes (default; the
+    // column pass warp-local where it applies).  SPGPE_COLPASS=tma or warp
+    // picks between the two persistent column passes.  spgpe_autotune
+    // overrides both.
     const char *env = std::getenv("SPGPE_PERSISTENT");
     if (env && env[0] >= '0' && env[0] <= '2') {
       c->persistent_col = env[0] != '0';
       c->persistent_row = env[0] == '2';
+      c->warp_col = env[0] != '0';
     }
+    const char *cp = std::getenv("SPGPE_COLPASS");
+    if (cp && std::strcmp(cp, "warp") == 0) c->warp_col = true;
+    if (cp && std::strcmp(cp, "tma") == 0) c->warp_col = false;
   }
   {
     const int lx = log2i(nx), ly = log2i(ny), esz = (int)es;
@@ -819,8 +848,12 @@ int spgpe_init_multi(spgpe_ctx **out, int nclass, const int *nx, const int *ny, 
     c->cls.push_back(kc);
     if (cudaEventCreateWithFlags(&kc->join_ev, cudaEventDisableTiming) != cudaSuccess)
       return bail(SPGPE_ECUDA, "cudaEventCreate failed");
-    // the persistent passes of the classes share the GPU in proportion to their points
-    if (sms > 0) kc->sms = std::max(1, (int)std::lround(sms * (double)ninst[k] * nx[k] * ny[k] / work));
+    // The persistent passes of a class are sized to a share of the GPU:
+    // SPGPE_CLASS_SMS=share gives each class the SMs in proportion to its
+    // points, the default (full) every SM, the classes then interleaving.
+    const char *mode = std::getenv("SPGPE_CLASS_SMS");
+    if (sms > 0 && mode && std::strcmp(mode, "share") == 0)
+      kc->sms = std::max(1, (int)std::lround(sms * (double)ninst[k] * nx[k] * ny[k] / work));
     c->cls_first.push_back(first);
     c->cls_off.push_back(off);
     first += ninst[k];
@@ -1224,6 +1257,7 @@ int ensure_twin(spgpe_ctx *c) {
     if (r) return fail(c, r, "complex64 twin: " + g_init_error);
     t->persistent_row = c->persistent_row;
     t->persistent_col = c->persistent_col;
+    t->warp_col = c->warp_col;
     c->twin = t;
   }
   spgpe_ctx *t = c->twin;
@@ -1494,13 +1528,19 @@ extern "C" int spgpe_autotune(spgpe_ctx *c, const void *psi, double dt, int *cho
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
-    // each variant timed kReps times, the variants interleaved; the minimum counts
-    float vms[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+    // each variant timed kReps times, the variants interleaved; the minimum
+    // counts.  Variant v: bit 0 persistent row pass; v >> 1 the column pass
+    // (0 plain, 1 persistent TMA, 2 warp-local, where it applies).
+    const int nv = warp_col_applies(m) ? 6 : 4;
+    float vms[6] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    auto set_variant = [](spgpe_ctx *x, int v) {
+      x->persistent_row = (v & 1) != 0;
+      x->persistent_col = (v >> 1) == 1;
+      x->warp_col = (v >> 1) == 2;
+    };
     for (int rep = 0; rep < kReps && !r; ++rep)
-      for (int v = 0; v < 4 && !r; ++v) {
-        // variant v: bit 0 persistent row pass, bit 1 persistent column pass
-        m->persistent_row = (v & 1) != 0;
-        m->persistent_col = (v & 2) != 0;
+      for (int v = 0; v < nv && !r; ++v) {
+        set_variant(m, v);
         cudaError_t e = cudaMemcpyAsync(m->d_scratch, mem[k].p, m->psi_bytes(), cudaMemcpyDeviceToDevice, m->st);
         if (e != cudaSuccess) {
           r = cuda_fail(c, e, "autotune copy");
@@ -1524,15 +1564,11 @@ extern "C" int spgpe_autotune(spgpe_ctx *c, const void *psi, double dt, int *cho
     cudaEventDestroy(e1);
     if (r) return r == SPGPE_ECUDA ? r : fail(c, r, m->err);
     int best = 0;
-    for (int v = 1; v < 4; ++v)
+    for (int v = 1; v < nv; ++v)
       if (vms[v] < vms[best]) best = v;
     const float best_ms = vms[best];
-    m->persistent_row = (best & 1) != 0;
-    m->persistent_col = (best & 2) != 0;
-    if (m->twin) {
-      m->twin->persistent_row = m->persistent_row;
-      m->twin->persistent_col = m->persistent_col;
-    }
+    set_variant(m, best);
+    if (m->twin) set_variant(m->twin, best);
     if (choice_out) choice_out[k] = best;
     if (ms_out) ms_out[k] = best_ms / kTimed;
   }

@@ -79,4 +79,18 @@ __device__ __forceinline__ void tma_g2s_2d(void *dst, const CUtensorMap *map, in
       : "memory");
 }
 
+// 2D tile shared -> global through a tensor map (bulk-group completion):
+// issue, then commit; bulk_wait_read0 waits until every committed store has
+// finished reading shared memory (the buffer may then be overwritten).
+__device__ __forceinline__ void tma_s2g_2d(const CUtensorMap *map, int x, int y, const void *src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_addr(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed bulk store complete (its writes performed)
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 }  // namespace spgpe

@@ -139,6 +139,10 @@ template <class T> cudaError_t launch_row_p(int flags, RowArgs a, cudaStream_t s
 template <class T> int colp_cols(int nx, int ny);
 template <class T> cudaError_t launch_col_p(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t s, int sms);
 template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t s);
+// Warp-local column pass (complex64, ny = 256, nx >= 16; otherwise
+// cudaErrorNotSupported): psi through `map`, a tensor map like the one above
+// but with 16 x 256 boxes and the 128-byte swizzle.
+template <class T> cudaError_t launch_col_w(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t s, int sms);
 // Geometry of the Sec. 6 observables: grid, radial bin width h and count nb.
 struct ObsGeom {
   int nx, ny, nb;

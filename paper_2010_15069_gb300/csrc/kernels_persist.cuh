@@ -325,4 +325,126 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
   }
 }
 
+// ------------------------------------ warp-local column pass (256 rows, c64)
+//
+// Tiles of 16 columns x 256 rows of one component arrive by TMA with the
+// 128-byte swizzle: row r of a tile is one 128-byte line whose 16-byte chunks
+// (two columns each) are permuted by chunk ^ (r & 7).  Each warp owns two
+// adjacent columns; its lane l holds column 2w + ((l >> 3) & 1) at positions
+// t + 16 m, t = (l & 7) + 8 (l >> 4), so each half-warp touches 8 consecutive
+// rows of both columns: all 32 banks once, for the tile reads and the result
+// writes alike.  The FFT exchanges run in a per-warp padded area (column
+// stride 280 elements, one pad per 16) under warp barriers only; the results
+// go back into the tile in place and leave by one TMA store of the tile.  Per
+// tile the block meets two barriers: after the load lands, before the store.
+
+constexpr int kColW_C = 16, kColW_N = 256, kColW_TT = 16;
+constexpr int kColW_XS = 280;  // exchange elements per column (256 + 16 pads + 8 bank shift)
+constexpr size_t kColW_Tile = (size_t)kColW_N * kColW_C * 8;  // 32 KiB, 1 KiB aligned
+
+__host__ __device__ constexpr size_t colw_smem() {
+  return 1024 + 128 /* alignment slack, margin */ + 2 * kColW_Tile + (size_t)8 * 2 * kColW_XS * 8 + kColW_N * 8 + 2 * 8;
+}
+
+struct ColAccW {
+  cx<float> *base;  // this column's exchange area
+  __device__ __forceinline__ void st(int, int p, cx<float> v) const { base[p + (p >> 4)] = v; }
+  __device__ __forceinline__ cx<float> ld(int, int p) const { return base[p + (p >> 4)]; }
+  __device__ __forceinline__ static void sync() { __syncwarp(); }
+};
+
+// byte offset of (row r, column c) in a swizzled tile
+__device__ __forceinline__ uint32_t sw_off(int r, int c) {
+  return (uint32_t)r * 128u + ((uint32_t)((c >> 1) ^ (r & 7)) << 4) + ((uint32_t)(c & 1) << 3);
+}
+
+template <bool IMAG>
+__global__ void __launch_bounds__(256, 2)
+    col_pass_w(const __grid_constant__ CUtensorMap map, const ColArgs a, int ntiles) {
+  constexpr int N = kColW_N, E = 16, TT = kColW_TT, C = kColW_C;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char *tiles = sm;
+  cx<float> *xch = reinterpret_cast<cx<float> *>(sm + 2 * kColW_Tile);
+  cx<float> *btab = xch + 8 * 2 * kColW_XS;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(btab + N);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cl = (lane >> 3) & 1;                 // column within the warp's pair
+  const int c = 2 * w + cl;                       // column within the tile
+  const int t = (lane & 7) + 8 * (lane >> 4);     // position index within the column
+  const int cgroups = a.nx / C;
+  const ColAccW acc{xch + (w * 2 + cl) * kColW_XS};
+
+  auto next_active = [&](int v) {
+    if (a.active)
+      while (v < ntiles && !a.active[v / (2 * cgroups)]) v += gridDim.x;
+    return v;
+  };
+  auto issue = [&](int tile, int s) {
+    const int pc = tile / cgroups, cg = tile - pc * cgroups;
+    mbar_expect_tx(&bar[s], (uint32_t)kColW_Tile);
+    tma_g2s_2d(tiles + s * kColW_Tile, &map, cg * C, pc * N, &bar[s]);
+  };
+  int tile = next_active(blockIdx.x);
+  int nxt = tile < ntiles ? next_active(tile + gridDim.x) : ntiles;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+    if (tile < ntiles) issue(tile, 0);
+    if (nxt < ntiles) issue(nxt, 1);
+  }
+  for (int k = threadIdx.x; k < N; k += blockDim.x) btab[k] = reinterpret_cast<const cx<float> *>(a.kyt)[k];
+  __syncthreads();
+  const float inv = a.inv_f;
+  int refill = ntiles, refill_s = 0;  // a buffer whose store must finish reading before its reload
+  for (int i = 0; tile < ntiles; ++i) {
+    const int s = i & 1;
+    const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((i >> 1) & 1));
+    if (!__syncthreads_and(ok)) {
+      // loads still in flight: this buffer's, and the other's on the first
+      // tile only (later reloads of the other buffer are not yet issued here)
+      if (threadIdx.x == 0) {
+        atomicOr(a.flags, kErrTimeout);
+        mbar_wait_bounded(&bar[s], (uint32_t)((i >> 1) & 1));
+        if (nxt < ntiles && refill == ntiles) mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+        bulk_wait0();
+      }
+      return;
+    }
+    // the previous tile's store has had this tile's wait to read its buffer
+    if (threadIdx.x == 0 && refill < ntiles) {
+      bulk_wait_read0();
+      issue(refill, refill_s);
+    }
+    refill = ntiles;    unsigned char *tb = tiles + s * kColW_Tile;
+    const int pc = tile / cgroups, kx = (tile - pc * cgroups) * C + c;
+    cx<float> v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[0][m] = *reinterpret_cast<const cx<float> *>(tb + sw_off(t + m * TT, c));
+    const cx<float> am = reinterpret_cast<const cx<float> *>(a.kxt)[(long)pc * a.nx + kx];
+    col_compute<float, 8, 4, IMAG>(v, t, acc, a.tw, am, btab, inv);
+    // results in place (this warp's columns only), then one store of the tile
+#pragma unroll
+    for (int m = 0; m < E; ++m) *reinterpret_cast<cx<float> *>(tb + sw_off(t + m * TT, c)) = v[0][m];
+    fence_proxy_async();
+    __syncthreads();
+    const int after = nxt < ntiles ? next_active(nxt + gridDim.x) : ntiles;
+    if (threadIdx.x == 0) {
+      const int cg = tile - pc * cgroups;
+      tma_s2g_2d(&map, cg * C, pc * N, tb);
+      bulk_commit();
+    }
+    // buffer s is reloaded (with `after`, which exists only if nxt does) once
+    // its store has read it: at the next tile's start
+    if (after < ntiles) {
+      refill = after;
+      refill_s = s;
+    }
+    tile = nxt;
+    nxt = after;
+  }
+  if (threadIdx.x == 0) bulk_wait0();
+}
+
 }  // namespace spgpe

@@ -192,6 +192,28 @@ template <class T> cudaError_t launch_col_p(bool imag, ColArgs a, const CUtensor
 #undef SPGPE_COLP_IMAG
 }
 
+// ---- warp-local column pass (ny = 256, complex64; psi viewed through a
+// 128-byte-swizzled tensor map with 16 x 256 boxes)
+
+template <bool IMAG> cudaError_t colw_launch(ColArgs a, const CUtensorMap &map, cudaStream_t st, int sms) {
+  auto kern = col_pass_w<IMAG>;
+  const size_t smem = colw_smem();
+  static int granted = 0, occ = -1;  // per instantiation (per time direction)
+  cudaError_t e = grant_smem_c(kern, smem, granted);
+  if (e != cudaSuccess) return e;
+  if (occ < 0 && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem)) != cudaSuccess) return e;
+  const int ntiles = (a.nx / kColW_C) * 2 * a.ninst;
+  const int grid = std::max(1, std::min(ntiles, std::max(1, occ) * sms));
+  a.C = kColW_C;
+  kern<<<grid, 256, smem, st>>>(map, a, ntiles);
+  return cudaGetLastError();
+}
+
+template <class T> cudaError_t launch_col_w(bool imag, ColArgs a, const CUtensorMap &map, cudaStream_t st, int sms) {
+  if (sizeof(T) != 4 || a.ny != kColW_N || a.nx < kColW_C) return cudaErrorNotSupported;
+  return imag ? colw_launch<true>(a, map, st, sms) : colw_launch<false>(a, map, st, sms);
+}
+
 template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t st) {
   const long plane = (long)a.nx * a.ny;
   ref_K_kernel<T><<<dim3((unsigned)((plane + 255) / 256), 2 * a.ninst), 256, 0, st>>>(a);
@@ -207,6 +229,7 @@ template <class T> cudaError_t launch_ref_K(const ColArgs &a, cudaStream_t st) {
                                           cudaStream_t);                                      \
   template cudaError_t launch_ref_K<T>(const ColArgs &, cudaStream_t);                      \
   template int colp_cols<T>(int, int);                                                        \
-  template cudaError_t launch_col_p<T>(bool, ColArgs, const CUtensorMap &, cudaStream_t, int);
+  template cudaError_t launch_col_p<T>(bool, ColArgs, const CUtensorMap &, cudaStream_t, int);     \
+  template cudaError_t launch_col_w<T>(bool, ColArgs, const CUtensorMap &, cudaStream_t, int);
 
 }  // namespace spgpe

@@ -252,6 +252,33 @@ def test_persistent_and_plain_row_passes_agree(dtype, nx, ny, ninst, monkeypatch
     assert np.abs(out["0"][1] - out["2"][1]).max() < tol
 
 
+@pytest.mark.parametrize("nx,ninst", [(16, 3), (64, 2), (256, 2), (512, 1)])
+def test_column_pass_variants_agree(nx, ninst, monkeypatch):
+    """The column pass as one tile per block, as the persistent TMA pass and as
+    the warp-local TMA pass (128-byte swizzle, ny = 256, complex64): same
+    arithmetic, so the same bits in real time, and in imaginary time between
+    the two TMA passes (both beside the persistent row pass; the plain row
+    pass groups the FP64 atom-number sums differently)."""
+    p = coupled(nx, 256)
+    psi0 = np.stack([inputs.gaussian_spinor(p.grid, seed=30 + i) for i in range(ninst)])
+    out = {}
+    for name, env in (("plain", {"SPGPE_PERSISTENT": "0"}), ("tma", {"SPGPE_PERSISTENT": "2", "SPGPE_COLPASS": "tma"}),
+                      ("warp", {"SPGPE_PERSISTENT": "2", "SPGPE_COLPASS": "warp"})):
+        monkeypatch.delenv("SPGPE_COLPASS", raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        with ctx_for(p, "c64", ninst=ninst) as c:
+            a = to_dev(psi0, "c64")
+            c.step_real(a, 1e-3, 6)
+            b = a.clone()
+            c.step_imag(b, 1e-3, 5, sp.SPGPE_NORM_TOTAL)
+            out[name] = (to_host(a), to_host(b))
+    for name in ("tma", "warp"):
+        assert np.array_equal(out[name][0], out["plain"][0]), name
+    assert np.array_equal(out["warp"][1], out["tma"][1])
+    assert np.abs(out["tma"][1] - out["plain"][1]).max() < 2e-6
+
+
 def test_cufft_comparator_matches_oracle(orc):
     p = coupled(64, 64)
     psi0 = inputs.gaussian_spinor(p.grid, seed=9)
