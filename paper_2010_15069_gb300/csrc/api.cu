@@ -83,7 +83,13 @@ struct spgpe_ctx {
   bool persistent_col = true;
   bool warp_col = true;  // the warp-local column pass where it applies (ny = 256, complex64)
   const void *map_psi = nullptr, *map_sw_psi = nullptr;
+  int map_ninst = 0, map_sw_ninst = 0;
   CUtensorMap map{}, map_sw{};
+  // Host spinors of a batch go through in chunks of instances: copies in on
+  // cp_in, the steps on st, copies out on cp_out (streams and events created
+  // on first use).
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_done;
   void *d_gparT = nullptr;
 
   // Batch over several grid sizes: the size classes are child contexts, each
@@ -182,6 +188,10 @@ void free_all(spgpe_ctx *c) {
     free_all(k);
     delete k;
   }
+  for (cudaEvent_t e : c->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_done) cudaEventDestroy(e);
+  if (c->cp_in) cudaStreamDestroy(c->cp_in);
+  if (c->cp_out) cudaStreamDestroy(c->cp_out);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -400,6 +410,37 @@ RowArgs row_args(spgpe_ctx *c, void *psi, double dt) {
   return a;
 }
 
+// The same arguments for instances i0 .. i0 + ni - 1 only: psi and every
+// per-instance table seen from instance i0 (the kernels index instances
+// from zero); psi is the batch's base pointer.
+template <class P> P *skip(P *p, size_t bytes) {
+  return p ? reinterpret_cast<P *>(reinterpret_cast<unsigned char *>(const_cast<void *>(static_cast<const void *>(p))) +
+                                   bytes)
+           : p;
+}
+
+void restrict_row(const spgpe_ctx *c, RowArgs &a, int i0, int ni) {
+  const size_t es = c->es, i = (size_t)i0;
+  a.psi = skip(a.psi, i * 2 * c->plane() * es);
+  a.tabx = skip(a.tabx, i * c->nx * 2 * es);
+  a.taby = skip(a.taby, i * c->ny * 2 * es);
+  a.gpar = skip(a.gpar, i * 4 * sizeof(double));
+  a.gparT = skip(a.gparT, i * 4 * (es / 2));
+  a.partials = skip(a.partials, i * c->ny * 2 * sizeof(double));
+  a.counters = skip(a.counters, i * sizeof(unsigned));
+  a.scale = skip(a.scale, i * 2 * sizeof(double));
+  a.active = skip(a.active, i * sizeof(int));
+  a.ninst = ni;
+}
+
+void restrict_col(const spgpe_ctx *c, ColArgs &a, int i0, int ni) {
+  const size_t es = c->es, i = (size_t)i0;
+  a.psi = skip(a.psi, i * 2 * c->plane() * es);
+  a.kxt = skip(a.kxt, i * 2 * c->nx * es);
+  a.active = skip(a.active, i * sizeof(int));
+  a.ninst = ni;
+}
+
 ColArgs col_args(spgpe_ctx *c, void *psi) {
   ColArgs a{};
   a.psi = psi;
@@ -471,7 +512,7 @@ cudaError_t row(spgpe_ctx *c, int flags, const RowArgs &a) {
 // (8-byte elements: one complex64, or half a complex128): `map` with boxes
 // of C complex columns by min(ny, 256) rows for the persistent column pass,
 // `map_sw` with 16 x 256 boxes and the 128-byte swizzle for the warp-local one.
-cudaError_t encode_map(spgpe_ctx *c, const void *psi, CUtensorMap *m, int cols, bool swizzle) {
+cudaError_t encode_map(spgpe_ctx *c, const void *psi, int ninst, CUtensorMap *m, int cols, bool swizzle) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -481,7 +522,7 @@ cudaError_t encode_map(spgpe_ctx *c, const void *psi, CUtensorMap *m, int cols, 
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const int xm = c->dtype == SPGPE_C64 ? 1 : 2;
-  const cuuint64_t dims[2] = {(cuuint64_t)c->nx * xm, (cuuint64_t)c->ninst * 2 * c->ny};
+  const cuuint64_t dims[2] = {(cuuint64_t)c->nx * xm, (cuuint64_t)ninst * 2 * c->ny};
   const cuuint64_t strides[1] = {(cuuint64_t)c->nx * c->es};
   const cuuint32_t box[2] = {(cuuint32_t)(cols * xm), (cuuint32_t)std::min(c->ny, 256)};
   const cuuint32_t estr[2] = {1, 1};
@@ -492,18 +533,24 @@ cudaError_t encode_map(spgpe_ctx *c, const void *psi, CUtensorMap *m, int cols, 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t ensure_map(spgpe_ctx *c, const void *psi) {
-  if (c->map_psi == psi) return cudaSuccess;
+cudaError_t ensure_map(spgpe_ctx *c, const void *psi, int ninst) {
+  if (c->map_psi == psi && c->map_ninst == ninst) return cudaSuccess;
   const int C = c->dtype == SPGPE_C64 ? colp_cols<float>(c->nx, c->ny) : colp_cols<double>(c->nx, c->ny);
-  const cudaError_t e = encode_map(c, psi, &c->map, C, false);
-  if (e == cudaSuccess) c->map_psi = psi;
+  const cudaError_t e = encode_map(c, psi, ninst, &c->map, C, false);
+  if (e == cudaSuccess) {
+    c->map_psi = psi;
+    c->map_ninst = ninst;
+  }
   return e;
 }
 
-cudaError_t ensure_map_sw(spgpe_ctx *c, const void *psi) {
-  if (c->map_sw_psi == psi) return cudaSuccess;
-  const cudaError_t e = encode_map(c, psi, &c->map_sw, 16, true);
-  if (e == cudaSuccess) c->map_sw_psi = psi;
+cudaError_t ensure_map_sw(spgpe_ctx *c, const void *psi, int ninst) {
+  if (c->map_sw_psi == psi && c->map_sw_ninst == ninst) return cudaSuccess;
+  const cudaError_t e = encode_map(c, psi, ninst, &c->map_sw, 16, true);
+  if (e == cudaSuccess) {
+    c->map_sw_psi = psi;
+    c->map_sw_ninst = ninst;
+  }
   return e;
 }
 
@@ -512,9 +559,9 @@ bool warp_col_applies(const spgpe_ctx *c) { return c->dtype == SPGPE_C64 && c->n
 cudaError_t col(spgpe_ctx *c, bool imag, const ColArgs &a) {
   const bool ok16 = c->sms > 0 && aligned16(a.psi);
   bool w = c->warp_col && ok16 && warp_col_applies(c);
-  if (w && ensure_map_sw(c, a.psi) != cudaSuccess) w = false;
+  if (w && ensure_map_sw(c, a.psi, a.ninst) != cudaSuccess) w = false;
   bool p = !w && c->persistent_col && ok16;
-  if (p && ensure_map(c, a.psi) != cudaSuccess) p = false;
+  if (p && ensure_map(c, a.psi, a.ninst) != cudaSuccess) p = false;
   return timed(c, imag ? 8 : 3, [&] {
     if (w) {
       const cudaError_t e = launch_col_w<float>(imag, a, c->map_sw, c->st, c->sms);
@@ -556,6 +603,48 @@ int begin_psi(spgpe_ctx *c, const void *psi, void **dev, bool *host) {
 int end_psi(spgpe_ctx *c, void *psi, bool host) {
   if (!host) return SPGPE_OK;
   CK(c, cudaMemcpyAsync(psi, c->d_stage, c->psi_bytes(), cudaMemcpyDeviceToHost, c->st));
+  CK(c, cudaStreamSynchronize(c->st));
+  return SPGPE_OK;
+}
+
+// Host spinor of a batch: copy in, step and copy out in chunks of instances,
+// the copy in of a chunk (cp_in) and the copy out of the one before
+// (cp_out) overlapping the steps of another (on st).  run(i0, ni, base)
+// queues the steps of instances i0 .. i0 + ni - 1 of the staged batch at
+// `base` on st.  Synchronises.
+constexpr int kHostChunks = 8;
+template <class F> int host_pipeline(spgpe_ctx *c, void *psi, F &&run) {
+  const int nch = std::min(c->ninst, kHostChunks);
+  int r = dev_alloc(c, &c->d_stage, c->psi_bytes());
+  if (r) return r;
+  if (!c->cp_in) {
+    CK(c, cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
+    CK(c, cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
+  }
+  while ((int)c->ev_in.size() < nch + 1) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(c, cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    CK(c, cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    c->ev_in.push_back(a);
+    c->ev_done.push_back(b);
+  }
+  // the copies start after the work already queued on the context's stream
+  CK(c, cudaEventRecord(c->ev_done[nch], c->st));
+  CK(c, cudaStreamWaitEvent(c->cp_in, c->ev_done[nch], 0));
+  const size_t per = 2 * (size_t)c->plane() * c->es;
+  unsigned char *dev = static_cast<unsigned char *>(c->d_stage), *hst = static_cast<unsigned char *>(psi);
+  for (int k = 0; k < nch; ++k) {
+    const int i0 = (int)((long)k * c->ninst / nch), i1 = (int)((long)(k + 1) * c->ninst / nch);
+    const size_t off = (size_t)i0 * per, bytes = (size_t)(i1 - i0) * per;
+    CK(c, cudaMemcpyAsync(dev + off, hst + off, bytes, cudaMemcpyHostToDevice, c->cp_in));
+    CK(c, cudaEventRecord(c->ev_in[k], c->cp_in));
+    CK(c, cudaStreamWaitEvent(c->st, c->ev_in[k], 0));
+    if ((r = run(i0, i1 - i0, c->d_stage))) return r;
+    CK(c, cudaEventRecord(c->ev_done[k], c->st));
+    CK(c, cudaStreamWaitEvent(c->cp_out, c->ev_done[k], 0));
+    CK(c, cudaMemcpyAsync(hst + off, dev + off, bytes, cudaMemcpyDeviceToHost, c->cp_out));
+  }
+  CK(c, cudaStreamSynchronize(c->cp_out));
   CK(c, cudaStreamSynchronize(c->st));
   return SPGPE_OK;
 }
@@ -673,7 +762,7 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
 // residual partials (||Psi_{n+1} - Psi_n||^2, ||Psi_n||^2 per block and
 // instance) in d_partials for imag_collect.
 int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, double t0, double t1,
-                 bool residual) {
+                 bool residual, int i0 = 0, int ni = -1) {
   int r;
   if ((r = ensure_tables(c, dtau, 1))) return r;
   if (residual && (r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
@@ -681,7 +770,11 @@ int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, 
   ra.tgt0 = t0;
   ra.tgt1 = t1;
   ra.norm_mode = norm_mode;
-  const ColArgs ca = col_args(c, p);
+  ColArgs ca = col_args(c, p);
+  if (ni >= 0) {  // a chunk of instances (host pipeline; no residual)
+    restrict_row(c, ra, i0, ni);
+    restrict_col(c, ca, i0, ni);
+  }
   for (int s = 1; s <= nsteps; ++s) {
     if (s == nsteps && residual) {
       // Keep Psi_n (normalised) for the residual of the last step.
@@ -985,18 +1078,24 @@ int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
   if (!psi || nsteps < 0 || !std::isfinite(dt)) return fail(c, SPGPE_EINVAL, "bad psi, dt or nsteps");
   if (nsteps == 0) return SPGPE_OK;
   if ((r = ensure_tables(c, dt, 0))) return r;
-  void *p;
-  bool host;
-  if ((r = begin_psi(c, psi, &p, &host))) return r;
-  const RowArgs ra = row_args(c, p, dt);
-  const ColArgs ca = col_args(c, p);
-  CK(c, row(c, kRealFirst, ra));
-  for (int s = 1; s <= nsteps; ++s) {
-    CK(c, col(c, false, ca));
-    CK(c, row(c, s < nsteps ? kRealMid : kRealLast, ra));
+  // the steps of instances i0 .. i0 + ni - 1 of the batch at p
+  auto run = [&](int i0, int ni, void *p) -> int {
+    RowArgs ra = row_args(c, p, dt);
+    ColArgs ca = col_args(c, p);
+    restrict_row(c, ra, i0, ni);
+    restrict_col(c, ca, i0, ni);
+    CK(c, row(c, kRealFirst, ra));
+    for (int s = 1; s <= nsteps; ++s) {
+      CK(c, col(c, false, ca));
+      CK(c, row(c, s < nsteps ? kRealMid : kRealLast, ra));
+    }
+    return SPGPE_OK;
+  };
+  if (!is_device_ptr(psi)) {
+    if ((r = host_pipeline(c, psi, run))) return r;
+    return read_flags(c);
   }
-  if ((r = end_psi(c, psi, host))) return r;
-  return host ? read_flags(c) : SPGPE_OK;
+  return run(0, c->ninst, psi);
 }
 
 int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_mode, const double *target,
@@ -1042,6 +1141,12 @@ int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_m
     if (residual_out)
       for (int i = 0; i < c->ninst; ++i) residual_out[i] = NAN;
     return SPGPE_OK;
+  }
+  if (!residual_out && !is_device_ptr(psi)) {
+    r = host_pipeline(c, psi, [&](int i0, int ni, void *p) {
+      return imag_enqueue(c, p, dtau, nsteps, norm_mode, t0, t1, false, i0, ni);
+    });
+    return r ? r : read_flags(c);
   }
   void *p;
   bool host;

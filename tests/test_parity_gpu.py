@@ -208,6 +208,23 @@ def test_host_spinor_path_is_bit_identical(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_host_batch_goes_through_in_chunks_with_the_same_bits(dtype):
+    """A host spinor batch is copied in, stepped and copied out in chunks of
+    instances (uneven: 11 instances in 8 chunks) with the copies overlapping
+    the steps; the result equals stepping the batch on the device."""
+    p = coupled(64, 256)
+    psi0 = np.stack([inputs.gaussian_spinor(p.grid, seed=60 + i) for i in range(11)]).astype(NPT[dtype])
+    with ctx_for(p, dtype, ninst=11) as c:
+        t = to_dev(psi0, dtype)
+        c.step_real(t, 1e-3, 9)
+        c.step_imag(t, 1e-3, 4, sp.SPGPE_NORM_PER_COMPONENT)
+        h = psi0.copy()
+        c.step_real(h, 1e-3, 9)
+        c.step_imag(h, 1e-3, 4, sp.SPGPE_NORM_PER_COMPONENT)
+        assert np.array_equal(to_host(t), h.astype(np.complex128))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_split_runs_agree(dtype):
     """Real time: within a call the closing X(dt/4) of one step and the opening
     X(dt/4) of the next are applied as one rotation by the doubled angle; at a
