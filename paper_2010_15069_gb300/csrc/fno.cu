@@ -238,8 +238,8 @@ int forward(spgpe_fno *f, const float *a, int B, int n, float *out) {
   FCK(f, gemm_real(g, st));
   for (int l = 0; l < f->L; ++l) {
     float *v = f->vs[l], *u = f->us[l];
-    // along x: X1 = v Exr
-    FCK(f, gemm_real(rg(B * W * n, 2 * M, n, v, false, n, 1, f->Exr, 2 * M, 1, f->X1, 2 * M, 1), st));
+    // along x: X1 = v Exr, computed as X1^T = Exr^T v^T (the long side as N)
+    FCK(f, gemm_real(rg(2 * M, B * W * n, n, f->Exr, false, 1, 2 * M, v, 1, n, f->X1, 1, 2 * M), st));
     const float2 *X1c = reinterpret_cast<const float2 *>(f->X1);
     // along y: vh = Ey X1 per (sample, channel)
     FCK(f, gemm_complex(cg(2 * M, M, n, B * W, f->Ey, false, false, n, 1, 0, X1c, false, M, 1, n * M, f->vh[l], M, 1,
@@ -323,8 +323,8 @@ int gradient(spgpe_fno *f, const float *a, const float *target, int B, int n, fl
     g.sBb = WP;
     g.sCb = WP;
     FCK(f, gemm_real(g, st));
-    // spectral part: dG = du Exi^T (into X1), doh = Ey dG
-    FCK(f, gemm_real(rg(B * W * n, 2 * M, n, du, false, n, 1, f->Exi, 1, n, f->X1, 2 * M, 1), st));
+    // spectral part: dG = du Exi^T (into X1; as dG^T = Exi du^T), doh = Ey dG
+    FCK(f, gemm_real(rg(2 * M, B * W * n, n, f->Exi, false, n, 1, du, 1, n, f->X1, 1, 2 * M), st));
     const float2 *dG = reinterpret_cast<const float2 *>(f->X1);
     FCK(f, gemm_complex(cg(2 * M, M, n, B * W, f->Ey, false, false, n, 1, 0, dG, false, M, 1, n * M, f->doh, M, 1, SP),
                         st));

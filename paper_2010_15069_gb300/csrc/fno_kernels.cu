@@ -92,6 +92,111 @@ __global__ void __launch_bounds__(256) gemm_r(int M, int N, int K, int splits, i
   }
 }
 
+// The same product for large M and N: BM x 128 output tiles (BM = 64 or
+// 128), k steps of 8, each of the 256 threads accumulating (BM/16) x 8
+// outputs in registers: rows ty*R + i and (BM/2) + ty*R + i (R = BM/32),
+// columns tx*4 + j and 64 + tx*4 + j, so that the operand reads from shared
+// memory are float2/float4s that hit every bank once.  Same arguments and
+// split-K behaviour as gemm_r.
+template <class TA, int BM>
+__global__ void __launch_bounds__(256) gemm_r2(int M, int N, int K, int splits, int partial, float alpha,
+                                               const TA *__restrict__ A, long sAm, long sAk, long sAb,
+                                               const float *__restrict__ B, long sBk, long sBn, long sBb, float beta,
+                                               float *C, long sCm, long sCn, long sCb, long sCs,
+                                               const float *__restrict__ bias) {
+  constexpr int BN = 128, BK = 8, R = BM / 32;  // R rows per half of the thread's rows
+  __shared__ __align__(16) float As[BK][BM];
+  __shared__ __align__(16) float Bs[BK][BN];
+  const int bt = blockIdx.z / splits, sp = blockIdx.z - bt * splits;
+  const int ks = (K + splits - 1) / splits, k0 = sp * ks, k1 = min(K, k0 + ks);
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  A += bt * sAb;
+  B += bt * sBb;
+  float acc[2 * R][8];
+#pragma unroll
+  for (int i = 0; i < 2 * R; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  // tile loads walk along whichever index has unit stride (full sectors)
+  const bool a_m_fast = sAm == 1, b_k_fast = sBk == 1;
+  for (int kk = k0; kk < k1; kk += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int mm, k;
+      if (a_m_fast) {
+        k = e / BM;
+        mm = e - k * BM;
+      } else {
+        mm = e / BK;
+        k = e - mm * BK;
+      }
+      const int gm = m0 + mm, gk = kk + k;
+      As[k][mm] = (gm < M && gk < k1) ? to_f(A[gm * sAm + gk * sAk]) : 0.f;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+      int nn, k;
+      if (b_k_fast) {
+        nn = e / BK;
+        k = e - nn * BK;
+      } else {
+        k = e / BN;
+        nn = e - k * BN;
+      }
+      const int gn = n0 + nn, gk = kk + k;
+      Bs[k][nn] = (gn < N && gk < k1) ? B[gk * sBk + gn * sBn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      float a[2 * R], b[8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if constexpr (R == 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(&As[k][h * (BM / 2) + ty * R]);
+          a[h * R] = v.x;
+          a[h * R + 1] = v.y;
+          a[h * R + 2] = v.z;
+          a[h * R + 3] = v.w;
+        } else {
+          static_assert(R == 2, "BM is 64 or 128");
+          const float2 v = *reinterpret_cast<const float2 *>(&As[k][h * (BM / 2) + ty * R]);
+          a[h * R] = v.x;
+          a[h * R + 1] = v.y;
+        }
+      }
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[k][64 + tx * 4]);
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+      b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float *Cb = partial ? C + ((long)bt * splits + sp) * sCs : C + bt * sCb;
+#pragma unroll
+  for (int i = 0; i < 2 * R; ++i) {
+    const int gm = m0 + (i / R) * (BM / 2) + ty * R + (i % R);
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j / 4) * 64 + tx * 4 + (j % 4);
+      if (gn >= N) continue;
+      float *c = Cb + gm * sCm + gn * sCn;
+      if (partial) {
+        *c = acc[i][j];
+      } else {
+        float v = alpha * acc[i][j];
+        if (beta != 0.f) v = fmaf(beta, *c, v);
+        if (bias) v += bias[gm];
+        *c = v;
+      }
+    }
+  }
+}
+
 // out[i] (+)= sum_s part[s][i] in the order s = 0, 1, ...
 __global__ void reduce_splits(const float *__restrict__ part, long n, int splits, float *out, int accumulate) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -278,6 +383,24 @@ int grid_for(long n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4
 }  // namespace
 
 cudaError_t gemm_real(const GemmR &g, cudaStream_t st) {
+  // large products: the register-tiled kernel (BM = 128, or 64 when M is small)
+  if (g.N >= 128 && g.M >= 64) {
+    const int bm = g.M >= 128 ? 128 : 64;
+    const dim3 grid((g.N + 127) / 128, (g.M + bm - 1) / bm, g.batch * g.splits);
+#define SPGPE_R2(TA, BMV)                                                                                           \
+  gemm_r2<TA, BMV><<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.splits, g.partial ? 1 : 0, g.alpha,                     \
+                                         static_cast<const TA *>(g.A), g.sAm, g.sAk, g.sAb, g.B, g.sBk, g.sBn,     \
+                                         g.sBb, g.beta, g.C, g.sCm, g.sCn, g.sCb, g.sCs, g.bias)
+    if (g.a_bf16) {
+      if (bm == 128) SPGPE_R2(__nv_bfloat16, 128);
+      else SPGPE_R2(__nv_bfloat16, 64);
+    } else {
+      if (bm == 128) SPGPE_R2(float, 128);
+      else SPGPE_R2(float, 64);
+    }
+#undef SPGPE_R2
+    return cudaGetLastError();
+  }
   const dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.batch * g.splits);
   if (g.a_bf16)
     gemm_r<__nv_bfloat16><<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.splits, g.partial ? 1 : 0, g.alpha,
@@ -285,9 +408,8 @@ cudaError_t gemm_real(const GemmR &g, cudaStream_t st) {
                                                  g.sBk, g.sBn, g.sBb, g.beta, g.C, g.sCm, g.sCn, g.sCb, g.sCs, g.bias);
   else
     gemm_r<float><<<grid, 256, 0, st>>>(g.M, g.N, g.K, g.splits, g.partial ? 1 : 0, g.alpha,
-                                        static_cast<const float *>(g.A), g.sAm,
-                                        g.sAk, g.sAb, g.B, g.sBk, g.sBn, g.sBb, g.beta, g.C, g.sCm, g.sCn, g.sCb,
-                                        g.sCs, g.bias);
+                                        static_cast<const float *>(g.A), g.sAm, g.sAk, g.sAb, g.B, g.sBk, g.sBn,
+                                        g.sBb, g.beta, g.C, g.sCm, g.sCn, g.sCb, g.sCs, g.bias);
   return cudaGetLastError();
 }
 
