@@ -41,6 +41,7 @@ DT = 5e-4
 DEFAULT_INSTANCES = 256
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}  # read + write both components, one pass
 PASSES_PER_STEP = 2
+CUFFT_STEPS = 20
 
 
 def log(*a):
@@ -273,6 +274,66 @@ def sweep_throughput(steps=40):
             "ratio": t_seq / t_multi}
 
 
+# ------------------------------------------------------- single large instance
+
+SINGLE_SIZES = (2048, 4096)
+SINGLE_BOX = 24.0
+L2_BYTES = 129e6
+
+
+def single_instance(steps=200, cufft_steps=40):
+    """Real time on one large instance: 2048^2 (67 MB of complex64 spinor,
+    inside L2) and 4096^2 (268 MB, above it); box [-24, 24]^2, Omega = 2,
+    detuning slope 0.2, g11 = g22 = 1000, g12 = 900, kL = 1, dt = 5e-4, the
+    trap quenched to omega = 1.1 from a 20-vortex seeded state (seed 4; the
+    4096^2 state is the 2048^2 one interpolated spectrally).  The fused passes
+    (autotuned) against the cuFFT comparator on the same state (the paper's
+    step structure: cuFFT 2D transforms and separate elementwise kernels)."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    peak, _ = peaks()
+    stream = torch.cuda.Stream()
+    seed_state, out = None, []
+
+    def timed(run, k):
+        run(3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e-3
+
+    for n in SINGLE_SIZES:
+        p = inputs.problem(n, n, SINGLE_BOX, SINGLE_BOX, omega=1.1, Omega=2.0, delta_slope=0.2,
+                           g11=1000.0, g22=1000.0, g12=900.0, kL=1.0)
+        if seed_state is None:
+            seed_state = inputs.vortex_spinor(
+                inputs.problem(n, n, SINGLE_BOX, SINGLE_BOX).grid, n_vortices=20, radius=6.0, seed=4)
+            psi = seed_state
+        else:
+            psi = inputs.upsample_spectral(seed_state, n, n)
+        with sp.Context(n, n, SINGLE_BOX, SINGLE_BOX, "c64", ninst=1, stream=stream) as c:
+            c.set_potentials_separable(-1, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+            t = torch.from_numpy(np.ascontiguousarray(psi.astype(np.complex64))).cuda()
+            choice, _ = c.autotune(t, DT)
+            sec = timed(lambda k: c.step_real(t, DT, k), steps)
+            sec_ref = timed(lambda k: c.cufft_step_real(t, DT, k), cufft_steps)
+        nbytes = 2 * n * n * 8
+        fused = n * n * steps / sec
+        ref = n * n * cufft_steps / sec_ref
+        out.append({"grid": n, "spinor_mb": nbytes / 1e6, "l2_resident": nbytes < L2_BYTES,
+                    "fused_pt_steps_per_s": fused, "ms_per_step": sec / steps * 1e3,
+                    "step_frac": 2 * BYTES_PER_PT_PASS["c64"] * n * n * steps / sec / 1e9 / peak,
+                    "cufft_comparator_pt_steps_per_s": ref, "fused_over_cufft": fused / ref,
+                    "schedule": {"persistent_row": bool(choice[0] & 1),
+                                 "column_pass": ["plain", "persistent TMA", "warp-local TMA"][int(choice[0]) >> 1]}})
+    return {"workload": "one instance, real time, box [-24,24]^2, Omega=2, delta=0.2y, g=1000, g12=900, kL=1, "
+                        "dt=5e-4, trap quenched to omega=1.1, 20-vortex seeded state (seed 4), c64",
+            "steps": steps, "cufft_steps": cufft_steps, "sizes": out}
+
+
 # ------------------------------------------------------- warm-start network
 
 def fno_flops(n, cin=6, cout=4, W=64, M=32, L=4, H=128):
@@ -337,16 +398,48 @@ def oracle_rate(budget_s=12.0, max_steps=400):
     return NX * NY * n / dt, n, dt
 
 
+def _oracle_worker(seed, budget_s):
+    """One pool worker: oracle steps on its own instance for about budget_s."""
+    import oracle
+    p = inputs.config1(NX)
+    m = oracle.Model(NX, NY, 10.0, 10.0, V=p.V, delta=p.delta, Omega=p.Omega,
+                     g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+    psi = m.step(inputs.gaussian_spinor(p.grid, seed=seed), DT, 1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        psi = m.step(psi, DT, 10)
+        n += 10
+    return NX * NY * n, time.perf_counter() - t0
+
+
+def oracle_rate_all_cores(budget_s=8.0):
+    """The same oracle, one independent instance per host core in a spawned
+    process pool (the oracle itself is single-threaded and unchanged):
+    (aggregate pt-steps/s, workers, seconds)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_worker, [(i, budget_s) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    return sum(r[0] / r[1] for r in res), cores, wall
+
+
 KERNEL_SOURCES = ["fft_core.cuh", "kernels.cuh", "kernels_persist.cuh", "fastmath.cuh", "async_copy.cuh",
                   "internal.h", "launch_row.cuh", "launch_col.cuh"]
 
 
 def kernel_source_hash():
+    """Hash of the code of the kernel sources (line comments, trailing blanks
+    and empty lines left out, so that editing a comment keeps the profiles)."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2010_15069_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2010_15069_gb300", "csrc", f), encoding="utf-8") as fh:
+            for ln in fh:
+                code = ln.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -496,17 +589,31 @@ def run_fused(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * pts * e2e_steps / e2e_s
     psi_bytes = t.numel() * t.element_size()
+
+    # the paper's step structure on the same batch: cuFFT 2D transforms and
+    # separate elementwise kernels (a library comparator, not the product path)
+    c.cufft_step_real(t, DT, 3)
+    barrier()
+    start.record(stream)
+    c.cufft_step_real(t, DT, CUFFT_STEPS)
+    stop.record(stream)
+    barrier()
+    cufft_value = world * pts * CUFFT_STEPS / (start.elapsed_time(stop) * 1e-3)
     c.close()
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    cpu = None
+    cpu = cpu_all = None
     if world == 1:
         rate, n, el = oracle_rate()
         cpu = {"value": rate, "unit": "pt-steps/s", "cores": 1, "kind": "oracle",
                "sample": f"one 256x256 instance, {n} FP64 Strang steps in {el:.1f} s (single thread)"}
+        rate, cores, el = oracle_rate_all_cores()
+        cpu_all = {"value": rate, "unit": "pt-steps/s", "cores": cores, "kind": "oracle",
+                   "sample": f"one 256x256 instance per core, FP64 Strang steps for about 8 s each "
+                             f"({el:.1f} s wall), spawned process pool"}
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "pt-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -524,6 +631,11 @@ def run_fused(args):
                      "step_frac": (PASSES_PER_STEP * alg_bytes * args.steps / (ms * 1e-3) / 1e9) / peak},
         "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kt.items()},
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
+        "cufft_comparator": {"value": cufft_value, "unit": "pt-steps/s", "steps": CUFFT_STEPS,
+                             "what": "same batch and dt, cuFFT 2D C2C transforms + separate R and K kernels "
+                                     "(the paper's step structure)",
+                             "fused_over_cufft": value / cufft_value},
         "e2e": {"value": e2e_value, "unit": "pt-steps/s", "h2d_bytes_per_step": psi_bytes,
                 "d2h_bytes_per_step": psi_bytes, "steps": e2e_steps},
         "gpu_launches": launches,
@@ -531,6 +643,8 @@ def run_fused(args):
     }
     if world == 1 and args.ttr_instances > 0:
         line["time_to_residual"] = time_to_residual(args.ttr_instances)
+    if world == 1 and args.single:
+        line["single_instance"] = single_instance()
     if world == 1 and args.sweep:
         line["uneven_sweep"] = sweep_throughput()
     if world == 1 and args.fno:
@@ -557,6 +671,8 @@ def main():
     ap.add_argument("--schedule", choices=["auto", "persistent", "warp", "plain"], default="auto",
                     help="pass variants: autotuned (default) or fixed")
     ap.add_argument("--sweep", type=int, default=1, help="1: also time the uneven sweep batch (0: skip)")
+    ap.add_argument("--single", type=int, default=1,
+                    help="1: also time one 2048^2 and one 4096^2 instance against the cuFFT comparator (0: skip)")
     ap.add_argument("--fno", type=int, default=1, help="1: also time training of the warm-start FNO (0: skip)")
     ap.add_argument("--ttr-instances", type=int, default=8,
                     help="sweep instances of the time-to-residual comparison (0: skip it)")

@@ -224,7 +224,7 @@ std::vector<double> stage_twiddles(int logn, int loge, bool single) {
               g = -1.0;
               phi = th > 0 ? th - 0.5 * kTwoPi : th + 0.5 * kTwoPi;
             }
-            out.insert(out.end(), {std::tan(0.5 * phi), std::sin(phi), g, 0.0});
+            out.insert(out.end(), {std::tan(0.5 * phi), std::sin(phi), g, g});
           } else {
             out.insert(out.end(), {std::cos(kTwoPi * (double)m / n), -std::sin(kTwoPi * (double)m / n)});
           }

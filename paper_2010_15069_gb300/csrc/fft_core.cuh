@@ -29,6 +29,16 @@ template <class T> __device__ __forceinline__ T d_fma(T a, T b, T c) {
 }
 template <class T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
 template <class T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+// Single precision: one packed add of the (re, im) pair (sm_100 family
+// f32x2 arithmetic; each lane rounds exactly as the scalar add does).
+template <> __device__ __forceinline__ cx<float> cadd(cx<float> a, cx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(b.re, b.im));
+  return {r.x, r.y};
+}
+template <> __device__ __forceinline__ cx<float> csub(cx<float> a, cx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(-b.re, -b.im));
+  return {r.x, r.y};
+}
 template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
@@ -83,8 +93,9 @@ __device__ __forceinline__ cx<T> w16(cx<T> a) {
 // forward root exp(-2 pi i m / N) with m = r k N / (NS R).
 // Double precision: the root as a complex pair.  Single precision: the root
 // is g R(phi) with g = +-1 and R(phi) a rotation by phi in [-pi/2, pi/2],
-// stored as (tan(phi/2), sin(phi), g, 0) and applied with three shears and a
-// multiplication by g.  A single-precision (cos, sin) pair is off unit modulus
+// stored as (tan(phi/2), sin(phi), g, g) and applied with three shears and a
+// multiplication by g (one packed multiplication of the (re, im) pair by the
+// (g, g) half of the entry).  A single-precision (cos, sin) pair is off unit modulus
 // by about 2^-25 in a direction that does not average out over the set of
 // roots; every element passes through these factors in every transform, and
 // rounded pairs drain the norm by about 1e-7 per forward/inverse round trip.
@@ -97,7 +108,8 @@ __device__ __forceinline__ cx<T> twiddle(cx<T> u, const typename TwType<T>::type
   if constexpr (sizeof(T) == 4) {
     const float t = SIGN < 0 ? w.x : -w.x, s = SIGN < 0 ? w.y : -w.y;  // inverse: R(-phi)
     const cx<T> r = shear_rot(u, t, s);
-    return {r.re * w.z, r.im * w.z};
+    const float2 gr = __fmul2_rn(make_float2(r.re, r.im), make_float2(w.z, w.w));  // (g, g)
+    return {gr.x, gr.y};
   } else {
     const cx<T> c = SIGN < 0 ? w : cx<T>{w.re, -w.im};
     return cmul(u, c);

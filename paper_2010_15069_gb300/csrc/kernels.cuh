@@ -550,7 +550,12 @@ __device__ __forceinline__ void col_compute(cx<T> (&v)[1][1 << LOGE], int t, con
                         d_fma(am.re, b.im, d_fma(am.im, b.re, am.im + b.im))};
       z = add_mul1(z, k1);
     }
-    v[0][m] = {z.re * inv, z.im * inv};
+    if constexpr (sizeof(T) == 4) {
+      const float2 zi = __fmul2_rn(make_float2(z.re, z.im), make_float2(inv, inv));
+      v[0][m] = {zi.x, zi.y};
+    } else {
+      v[0][m] = {z.re * inv, z.im * inv};
+    }
   }
   block_fft<LOGN, LOGE, +1, 1>(v, t, tw, acc);
 }
