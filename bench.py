@@ -281,14 +281,15 @@ SINGLE_BOX = 24.0
 L2_BYTES = 129e6
 
 
-def single_instance(steps=200, cufft_steps=40):
+def single_instance(steps=200, cufft_steps=40, tune=True):
     """Real time on one large instance: 2048^2 (67 MB of complex64 spinor,
     inside L2) and 4096^2 (268 MB, above it); box [-24, 24]^2, Omega = 2,
     detuning slope 0.2, g11 = g22 = 1000, g12 = 900, kL = 1, dt = 5e-4, the
     trap quenched to omega = 1.1 from a 20-vortex seeded state (seed 4; the
     4096^2 state is the 2048^2 one interpolated spectrally).  The fused passes
-    (autotuned) against the cuFFT comparator on the same state (the paper's
-    step structure: cuFFT 2D transforms and separate elementwise kernels)."""
+    (autotuned unless the schedule is pinned) against the cuFFT comparator on
+    the same state (the paper's step structure: cuFFT 2D transforms and
+    separate elementwise kernels), with the fused passes' per-kernel times."""
     import torch
     import paper_2010_15069_gb300 as sp
     peak, _ = peaks()
@@ -317,8 +318,12 @@ def single_instance(steps=200, cufft_steps=40):
         with sp.Context(n, n, SINGLE_BOX, SINGLE_BOX, "c64", ninst=1, stream=stream) as c:
             c.set_potentials_separable(-1, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
             t = torch.from_numpy(np.ascontiguousarray(psi.astype(np.complex64))).cuda()
-            choice, _ = c.autotune(t, DT)
+            choice = c.autotune(t, DT)[0] if tune else None
             sec = timed(lambda k: c.step_real(t, DT, k), steps)
+            c.set_timing(True)
+            c.step_real(t, DT, steps)
+            kt = c.timing()
+            c.set_timing(False)
             sec_ref = timed(lambda k: c.cufft_step_real(t, DT, k), cufft_steps)
         nbytes = 2 * n * n * 8
         fused = n * n * steps / sec
@@ -327,8 +332,10 @@ def single_instance(steps=200, cufft_steps=40):
                     "fused_pt_steps_per_s": fused, "ms_per_step": sec / steps * 1e3,
                     "step_frac": 2 * BYTES_PER_PT_PASS["c64"] * n * n * steps / sec / 1e9 / peak,
                     "cufft_comparator_pt_steps_per_s": ref, "fused_over_cufft": fused / ref,
-                    "schedule": {"persistent_row": bool(choice[0] & 1),
-                                 "column_pass": ["plain", "persistent TMA", "warp-local TMA"][int(choice[0]) >> 1]}})
+                    "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kt.items()},
+                    "schedule": None if choice is None else
+                    {"persistent_row": bool(choice[0] & 1),
+                     "column_pass": ["plain", "persistent TMA", "warp-local TMA"][int(choice[0]) >> 1]}})
     return {"workload": "one instance, real time, box [-24,24]^2, Omega=2, delta=0.2y, g=1000, g12=900, kL=1, "
                         "dt=5e-4, trap quenched to omega=1.1, 20-vortex seeded state (seed 4), c64",
             "steps": steps, "cufft_steps": cufft_steps, "sizes": out}
@@ -644,7 +651,7 @@ def run_fused(args):
     if world == 1 and args.ttr_instances > 0:
         line["time_to_residual"] = time_to_residual(args.ttr_instances)
     if world == 1 and args.single:
-        line["single_instance"] = single_instance()
+        line["single_instance"] = single_instance(args.single_steps, tune=args.schedule == "auto")
     if world == 1 and args.sweep:
         line["uneven_sweep"] = sweep_throughput()
     if world == 1 and args.fno:
@@ -673,6 +680,7 @@ def main():
     ap.add_argument("--sweep", type=int, default=1, help="1: also time the uneven sweep batch (0: skip)")
     ap.add_argument("--single", type=int, default=1,
                     help="1: also time one 2048^2 and one 4096^2 instance against the cuFFT comparator (0: skip)")
+    ap.add_argument("--single-steps", type=int, default=200, help="timed steps of each single-instance run")
     ap.add_argument("--fno", type=int, default=1, help="1: also time training of the warm-start FNO (0: skip)")
     ap.add_argument("--ttr-instances", type=int, default=8,
                     help="sweep instances of the time-to-residual comparison (0: skip it)")

@@ -234,12 +234,14 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
 }
 
 // Columns per tile of the persistent column pass: a 128-byte row segment
-// where two tile buffers fit in about 110 KB and the block stays within 512
+// where two tile buffers fit in about 110 KB (160 KB for columns of 2048 rows
+// or more, which run one block per SM) and the block stays within 512
 // threads; at least 16 bytes (one TMA row of 8-byte elements).
 template <class T> __host__ __device__ constexpr int colp_cols_c(int logn, int loge) {
   const int n = 1 << logn, tt = n >> loge, es = (int)sizeof(cx<T>);
+  const size_t cap = (logn >= 11 ? 160 : 112) * 1024;
   int c = 128 / es;
-  while (c > 1 && (c * tt > kColMaxThreads || kPipe * colp_buf_bytes(n, c, es) > 112 * 1024)) c /= 2;
+  while (c > 1 && (c * tt > kColMaxThreads || kPipe * colp_buf_bytes(n, c, es) > cap)) c /= 2;
   if (c * es < 16) c = 16 / es;
   return c;
 }

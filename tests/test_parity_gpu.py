@@ -296,6 +296,27 @@ def test_column_pass_variants_agree(nx, ninst, monkeypatch):
     assert np.abs(out["tma"][1] - out["plain"][1]).max() < 2e-6
 
 
+@pytest.mark.parametrize("dtype,ny", [("c64", 2048), ("c64", 4096), ("c128", 2048), ("c128", 4096)])
+def test_tall_columns_against_oracle_and_plain_pass(orc, dtype, ny, monkeypatch):
+    """Columns of 2048 and 4096 rows (the persistent TMA column pass with a few
+    columns per tile and one 256-row box per 256 rows; 16 x ny, two instances):
+    real time against the oracle, and bit for bit against the plain pass."""
+    p = coupled(16, ny)
+    psi0 = np.stack([inputs.gaussian_spinor(p.grid, seed=50 + i) for i in range(2)])
+    out = {}
+    for mode in ("0", "2"):
+        monkeypatch.setenv("SPGPE_PERSISTENT", mode)
+        with ctx_for(p, dtype, ninst=2) as c:
+            a = to_dev(psi0, dtype)
+            c.step_real(a, 1e-3, 4)
+            out[mode] = to_host(a)
+    assert np.array_equal(out["0"], out["2"])
+    m = model_for(orc, p)
+    tol = c128_tol(4) if dtype == "c128" else 1e-5
+    for i in range(2):
+        assert np.abs(out["2"][i] - m.step(psi0[i], 1e-3, 4)).max() < tol
+
+
 def test_cufft_comparator_matches_oracle(orc):
     p = coupled(64, 64)
     psi0 = inputs.gaussian_spinor(p.grid, seed=9)
