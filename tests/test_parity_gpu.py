@@ -78,7 +78,8 @@ def ground0(orc):
 
 # ------------------------------------------------------------ real time
 
-@pytest.mark.parametrize("nx,ny", [(64, 64), (16, 128), (256, 32), (8, 8), (128, 64), (4096, 16), (16, 4096)])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (16, 128), (256, 32), (8, 8), (128, 64), (1024, 16), (4096, 16),
+                                   (16, 1024), (16, 4096)])
 @pytest.mark.parametrize("separable", [False, True])
 def test_real_time_c128_matches_oracle(orc, nx, ny, separable):
     p = coupled(nx, ny)
@@ -296,10 +297,12 @@ def test_column_pass_variants_agree(nx, ninst, monkeypatch):
     assert np.abs(out["tma"][1] - out["plain"][1]).max() < 2e-6
 
 
-@pytest.mark.parametrize("dtype,ny", [("c64", 2048), ("c64", 4096), ("c128", 2048), ("c128", 4096)])
+@pytest.mark.parametrize("dtype,ny", [("c64", 1024), ("c64", 2048), ("c64", 4096), ("c128", 1024), ("c128", 2048),
+                                      ("c128", 4096)])
 def test_tall_columns_against_oracle_and_plain_pass(orc, dtype, ny, monkeypatch):
-    """Columns of 2048 and 4096 rows (the persistent TMA column pass with a few
-    columns per tile and one 256-row box per 256 rows; 16 x ny, two instances):
+    """Columns of 1024 to 4096 rows (the persistent TMA column pass with a few
+    columns per tile and one 256-row box per 256 rows, and factored stage
+    twiddles from a span of 256 on; 16 x ny, two instances):
     real time against the oracle, and bit for bit against the plain pass."""
     p = coupled(16, ny)
     psi0 = np.stack([inputs.gaussian_spinor(p.grid, seed=50 + i) for i in range(2)])
