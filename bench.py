@@ -405,6 +405,40 @@ def oracle_rate(budget_s=12.0, max_steps=400):
     return NX * NY * n / dt, n, dt
 
 
+def copy_ceiling(t, reps=5):
+    """Pinned host <-> device copy rates of one batch-sized buffer, GB/s: in
+    alone, out alone, and both directions at once on two streams (the bound
+    of an end-to-end step that moves the batch in and out)."""
+    import torch
+    host_in = torch.empty(tuple(t.shape), dtype=t.dtype, pin_memory=True)
+    host_out = torch.empty(tuple(t.shape), dtype=t.dtype, pin_memory=True)
+    dev = torch.empty_like(t)
+    nbytes = t.numel() * t.element_size()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def h2d():
+        with torch.cuda.stream(s_in):
+            dev.copy_(host_in, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s_out):
+            host_out.copy_(t, non_blocking=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    t_in, t_out = timed(h2d), timed(d2h)
+    t_both = timed(lambda: (h2d(), d2h()))
+    return {"h2d_gbs": nbytes / t_in / 1e9, "d2h_gbs": nbytes / t_out / 1e9,
+            "both_directions_gbs": 2 * nbytes / t_both / 1e9, "bytes": nbytes}
+
+
 def _oracle_worker(seed, budget_s):
     """One pool worker: oracle steps on its own instance for about budget_s."""
     import oracle
@@ -596,6 +630,7 @@ def run_fused(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * pts * e2e_steps / e2e_s
     psi_bytes = t.numel() * t.element_size()
+    ceiling = copy_ceiling(t)
 
     # the paper's step structure on the same batch: cuFFT 2D transforms and
     # separate elementwise kernels (a library comparator, not the product path)
@@ -644,7 +679,9 @@ def run_fused(args):
                                      "(the paper's step structure)",
                              "fused_over_cufft": value / cufft_value},
         "e2e": {"value": e2e_value, "unit": "pt-steps/s", "h2d_bytes_per_step": psi_bytes,
-                "d2h_bytes_per_step": psi_bytes, "steps": e2e_steps},
+                "d2h_bytes_per_step": psi_bytes, "steps": e2e_steps,
+                "copy_gbs": 2 * psi_bytes * e2e_steps / e2e_s / 1e9, "copy_ceiling": ceiling,
+                "frac_of_copy_ceiling": 2 * psi_bytes * e2e_steps / e2e_s / 1e9 / ceiling["both_directions_gbs"]},
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }

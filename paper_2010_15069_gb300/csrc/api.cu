@@ -82,6 +82,7 @@ struct spgpe_ctx {
   bool persistent_row = true;
   bool persistent_col = true;
   bool warp_col = true;  // the warp-local column pass where it applies (ny = 256, complex64)
+  int host_chunks = 8;   // chunks of instances a host batch goes through (copies overlap steps)
   const void *map_psi = nullptr, *map_sw_psi = nullptr;
   int map_ninst = 0, map_sw_ninst = 0;
   CUtensorMap map{}, map_sw{};
@@ -612,9 +613,8 @@ int end_psi(spgpe_ctx *c, void *psi, bool host) {
 // (cp_out) overlapping the steps of another (on st).  run(i0, ni, base)
 // queues the steps of instances i0 .. i0 + ni - 1 of the staged batch at
 // `base` on st.  Synchronises.
-constexpr int kHostChunks = 8;
 template <class F> int host_pipeline(spgpe_ctx *c, void *psi, F &&run) {
-  const int nch = std::min(c->ninst, kHostChunks);
+  const int nch = std::min(c->ninst, c->host_chunks);
   int r = dev_alloc(c, &c->d_stage, c->psi_bytes());
   if (r) return r;
   if (!c->cp_in) {
@@ -733,6 +733,12 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
     const char *cp = std::getenv("SPGPE_COLPASS");
     if (cp && std::strcmp(cp, "warp") == 0) c->warp_col = true;
     if (cp && std::strcmp(cp, "tma") == 0) c->warp_col = false;
+    // SPGPE_HOST_CHUNKS: chunks of a host batch (1..64; default 8)
+    const char *hc = std::getenv("SPGPE_HOST_CHUNKS");
+    if (hc) {
+      const int v = std::atoi(hc);
+      if (v >= 1 && v <= 64) c->host_chunks = v;
+    }
   }
   {
     const int lx = log2i(nx), ly = log2i(ny), esz = (int)es;
