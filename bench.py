@@ -63,22 +63,45 @@ def ground_state_gpu():
         return t.cpu().numpy()
 
 
-def initial_states(B, ground):
+def initial_states(B, ground, first=0):
+    """psi0(i): instance first + i of the sweep (its phase noise is seeded by
+    that global index, so the ranks of a multi-GPU run step distinct
+    instances)."""
     base = inputs.upsample_spectral(ground, NX, NY)
 
     def psi0(i):
-        ph = 1e-3 * (2.0 * inputs.uniform01(1000 + i, 2 * NX * NY) - 1.0)
+        ph = 1e-3 * (2.0 * inputs.uniform01(1000 + first + i, 2 * NX * NY) - 1.0)
         return base * np.exp(1j * ph.reshape(2, NY, NX))
     return psi0
 
 
-def make_workload(B, dtype="c64", ground=None, stream=None):
-    """(context, device batch tensor, psi0(i)) of the benchmark workload."""
+def instance_range(rank, world, per_rank):
+    """(first, count) of the global instances rank `rank` of `world` steps:
+    weak scaling, each rank a disjoint slice of per_rank instances and no
+    data exchanged between ranks."""
+    if not 0 <= rank < world:
+        raise ValueError("rank out of range")
+    return rank * per_rank, per_rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The maximum of a per-rank scalar over all ranks (x itself on one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(B, dtype="c64", ground=None, stream=None, first=0):
+    """(context, device batch tensor, psi0(i)) of the benchmark workload:
+    instances first .. first + B - 1."""
     import torch
     import paper_2010_15069_gb300 as sp
     if ground is None:
         ground = ground_state_gpu()
-    psi0 = initial_states(B, ground)
+    psi0 = initial_states(B, ground, first)
     p = inputs.config1(NX)
     c = sp.Context(NX, NY, 10.0, 10.0, dtype, ninst=B, stream=stream)
     c.set_potentials_separable(-1, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
@@ -569,7 +592,8 @@ def run_fused(args):
     B, dtype = args.instances, args.dtype
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        c, t, _ = make_workload(B, dtype, stream=stream)
+        first, _ = instance_range(rank, world, B)
+        c, t, _ = make_workload(B, dtype, stream=stream, first=first)
     pts = B * NX * NY
     if args.schedule == "auto":
         # the library's autotuner picks the pass variants for this batch (scratch copy; psi unchanged)
@@ -596,11 +620,7 @@ def run_fused(args):
         stop.record(stream)
         launches = c.last_launches()
         barrier()
-    ms = start.elapsed_time(stop)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda")
     value = world * pts * args.steps / (ms * 1e-3)
 
     # per-kernel event timing over a second run of the same timed region
@@ -628,6 +648,8 @@ def run_fused(args):
     for _ in range(e2e_steps):
         c.step_real(hnp, DT, 1)
     e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e_value = world * pts * e2e_steps / e2e_s
     psi_bytes = t.numel() * t.element_size()
     ceiling = copy_ceiling(t)
@@ -640,7 +662,7 @@ def run_fused(args):
     c.cufft_step_real(t, DT, CUFFT_STEPS)
     stop.record(stream)
     barrier()
-    cufft_value = world * pts * CUFFT_STEPS / (start.elapsed_time(stop) * 1e-3)
+    cufft_value = world * pts * CUFFT_STEPS / (max_over_ranks(start.elapsed_time(stop), dist, "cuda") * 1e-3)
     c.close()
 
     if rank != 0:
