@@ -53,7 +53,7 @@ enum {
   SPGPE_ENOMEM = -2,     /* device or host allocation failed */
   SPGPE_ECUDA = -3,      /* a CUDA runtime call failed; see spgpe_last_error */
   SPGPE_ENONFINITE = -4, /* a norm or energy reduction met NaN/Inf (or a zero norm) */
-  SPGPE_ETIMEOUT = -5,   /* reserved: a bounded device wait gave up */
+  SPGPE_ETIMEOUT = -5,   /* a bounded device wait gave up (a tile transfer never landed) */
   SPGPE_ESTATE = -6      /* call out of order (e.g. stepping before potentials) */
 };
 
@@ -223,8 +223,18 @@ int spgpe_observables(spgpe_ctx *ctx, const void *psi, double *out);
 int spgpe_add_noise(spgpe_ctx *ctx, void *psi, double sigma, unsigned long long seed);
 
 /* Wait for the context's stream and report an error recorded on the device
- * by an earlier asynchronous step (ENONFINITE), clearing it. */
+ * by an earlier asynchronous step (ENONFINITE, ETIMEOUT), clearing it. */
 int spgpe_sync(spgpe_ctx *ctx);
+
+/* Probe of the bounded-wait failure path of the streaming passes: one kernel
+ * on the context's stream (the first size class of a multi-size context)
+ * waits, for about `cycles` SM clock cycles, on a shared-memory barrier that
+ * nothing completes, then records the timeout in the context's error flags
+ * and exits with nothing in flight, as a pass does when a tile transfer
+ * never lands.  Synchronises and returns what the next synchronising call
+ * would: ETIMEOUT (the flag is cleared and the context stays usable), or
+ * ECUDA if the launch failed.  EINVAL for cycles < 0. */
+int spgpe_wait_probe(spgpe_ctx *ctx, long long cycles);
 
 /* Comparator with the paper's structure (Sec. 4): the same S(dt) built from
  * cuFFT 2D transforms and separate elementwise kernels, several passes over

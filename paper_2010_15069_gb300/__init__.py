@@ -21,14 +21,14 @@ import ctypes
 import numpy as np
 
 from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SPGPE_RELAX_GIVE_UP,
-                   SPGPE_RELAX_LADDER, SpgpeError, check, load)
+                   SPGPE_RELAX_LADDER, SpgpeError, check, load, SPGPE_OK, SPGPE_ETIMEOUT)
 
 __all__ = [
-    "SPGPE_C64", "SPGPE_C128", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SPGPE_RELAX_GIVE_UP",
+    "SPGPE_C64", "SPGPE_C128", "SPGPE_OK", "SPGPE_ETIMEOUT", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SPGPE_RELAX_GIVE_UP",
     "SpgpeError",
     "Context", "FNO", "load",
     "spgpe_init_grid", "spgpe_init_batch", "spgpe_init_multi", "spgpe_set_potentials", "spgpe_set_potentials_separable",
-    "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_autotune", "spgpe_observables", "spgpe_add_noise", "spgpe_energy", "spgpe_norm", "spgpe_sync",
+    "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_autotune", "spgpe_observables", "spgpe_add_noise", "spgpe_energy", "spgpe_norm", "spgpe_sync", "spgpe_wait_probe",
     "spgpe_cufft_step_real", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
     "spgpe_last_launches", "spgpe_set_timing", "spgpe_timing",
 ]
@@ -150,6 +150,12 @@ def spgpe_norm(ctx, psi_ptr, ninst=1):
 
 def spgpe_sync(ctx):
     check(load().spgpe_sync(ctx), ctx)
+
+
+def spgpe_wait_probe(ctx, cycles):
+    """Run the bounded-wait failure probe; returns the status code (SPGPE_ETIMEOUT
+    when the wait gave up and was reported, as it should)."""
+    return int(load().spgpe_wait_probe(ctx, int(cycles)))
 
 
 def spgpe_cufft_step_real(ctx, psi_ptr, dt, nsteps):
@@ -421,6 +427,10 @@ class Context:
 
     def sync(self):
         spgpe_sync(self._ctx)
+
+    def wait_probe(self, cycles=1 << 20):
+        """Status code of the bounded-wait failure probe (SPGPE_ETIMEOUT expected)."""
+        return spgpe_wait_probe(self._ctx, cycles)
 
     def last_launches(self):
         return spgpe_last_launches(self._ctx)

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspgpe.so")
 SPGPE_C64, SPGPE_C128 = 1, 2
 SPGPE_NORM_TOTAL, SPGPE_NORM_PER_COMPONENT = 0, 1
 SPGPE_RELAX_LADDER, SPGPE_RELAX_GIVE_UP = 1, 2
+SPGPE_OK, SPGPE_ETIMEOUT = 0, -5
 STATUS = {0: "SPGPE_OK", -1: "SPGPE_EINVAL", -2: "SPGPE_ENOMEM", -3: "SPGPE_ECUDA",
           -4: "SPGPE_ENONFINITE", -5: "SPGPE_ETIMEOUT", -6: "SPGPE_ESTATE"}
 
@@ -31,6 +32,7 @@ SIGNATURES = {
     "spgpe_energy": (_I, [_P, _P, _P]),
     "spgpe_norm": (_I, [_P, _P, _P]),
     "spgpe_sync": (_I, [_P]),
+    "spgpe_wait_probe": (_I, [_P, ctypes.c_longlong]),
     "spgpe_cufft_step_real": (_I, [_P, _P, _D, _I]),
     "spgpe_destroy": (None, [_P]),
     "spgpe_last_error": (ctypes.c_char_p, [_P]),

@@ -15,6 +15,11 @@
 #include "spgpe.h"
 #include "internal.h"
 
+namespace spgpe {
+// The bounded-wait failure probe (kernels_misc.cu).
+cudaError_t launch_wait_probe(int *flags, long long budget, cudaStream_t s);
+}  // namespace spgpe
+
 using namespace spgpe;
 
 namespace {
@@ -1220,6 +1225,16 @@ int spgpe_sync(spgpe_ctx *c) {
   }
   CK(c, cudaStreamSynchronize(c->st));
   return read_flags(c);
+}
+
+int spgpe_wait_probe(spgpe_ctx *c, long long cycles) {
+  if (!c || cycles < 0) return c ? fail(c, SPGPE_EINVAL, "cycles must be >= 0") : SPGPE_EINVAL;
+  spgpe_ctx *k = c->cls.empty() ? c : c->cls[0];
+  CK(c, launch_wait_probe(k->d_flags, cycles, k->st));
+  CK(c, cudaStreamSynchronize(k->st));
+  const int r = read_flags(k);
+  if (r && k != c) return class_fail(c, k, r);
+  return r;
 }
 
 int spgpe_norm(spgpe_ctx *c, const void *psi, double *out) {

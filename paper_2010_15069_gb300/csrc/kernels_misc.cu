@@ -1,5 +1,7 @@
 // Precision conversion of spinors (the complex64 / complex128 ladder of
 // spgpe_relax): round complex128 to complex64, or widen complex64 exactly.
+// And the probe of the bounded-wait failure path.
+#include "async_copy.cuh"
 #include "internal.h"
 
 namespace spgpe {
@@ -30,6 +32,28 @@ cudaError_t launch_convert(const void *src, int src_es, void *dst, int dst_es, l
     widen_to_c128<<<grid, 256, 0, s>>>(reinterpret_cast<const float2 *>(src), reinterpret_cast<double2 *>(dst), n);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// Probe of the failure path the streaming passes take when a tile transfer
+// never lands: one thread arms an mbarrier that nothing will ever complete
+// (no copy is issued, no other thread arrives), waits on it with the given
+// cycle budget, and on giving up sets the timeout bit in the context's error
+// flags and returns, as the passes do.  Nothing is in flight when it leaves.
+__global__ void wait_probe(int *flags, long long budget) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  const long long t0 = clock64();
+  bool done = false;
+  while (!(done = mbar_try_wait(&bar, 0)) && clock64() - t0 <= budget) {
+  }
+  if (!done) atomicOr(flags, kErrTimeout);
+}
+
+cudaError_t launch_wait_probe(int *flags, long long budget, cudaStream_t s) {
+  wait_probe<<<1, 32, 0, s>>>(flags, budget);
   return cudaGetLastError();
 }
 

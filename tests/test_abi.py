@@ -52,6 +52,7 @@ def test_calls_on_null_context_are_rejected(lib):
     assert lib.spgpe_energy(None, None, None) == -1
     assert lib.spgpe_norm(None, None, None) == -1
     assert lib.spgpe_sync(None) == -1
+    assert lib.spgpe_wait_probe(None, 1) == -1
     assert lib.spgpe_last_launches(None) == 0
     lib.spgpe_destroy(None)
 
