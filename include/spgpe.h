@@ -245,8 +245,8 @@ int spgpe_cufft_step_real(spgpe_ctx *ctx, void *psi, double dt, int nsteps);
 /* ---- Learned warm start: a Fourier neural operator (FNO) ----
  * Not part of the paper's method: a network (the Fourier neural operator of
  * Li et al., arXiv:2010.08895) trained on ground states this library computes,
- * whose output seeds the imaginary-time relaxation of Sec. 3.2 (which stays
- * the judge of the result: spgpe_relax).  It maps input fields
+ * whose output seeds the imaginary-time relaxation of Sec. 3.2 (which still
+ * decides the result and its residual: spgpe_relax).  It maps input fields
  * a[batch][cin][n][n] to output fields out[batch][cout][n][n] (float32,
  * device memory, x fastest):
  *   v_0 = P a + p;  u_l = W_l v_l + w_l + S_l(v_l),  v_{l+1} = gelu(u_l)

@@ -1,6 +1,6 @@
 """What the learned warm start gains: an FNO trained on ground states the
 library computed proposes initial spinors for held-out parameter sets, and the
-plain imaginary-time relaxation (the judge of the result) needs fewer steps
+plain imaginary-time relaxation (which decides the result) needs fewer steps
 from them than from the vortex-seeded spinors of Sec. 6.
 """
 import numpy as np
