@@ -63,6 +63,10 @@ MUTANTS = {
 PIN_FILES = {name: "tests/test_oracle_observables.py" for name in
              ("separation_no_sqrt", "winding_clockwise", "contour_90_percent", "noise_variance_doubled",
               "splitmix_counter_from_zero")}
+# the same slips against the printed gauge-potential minima alone (test_oracle_golden.py)
+for _name in ("raman_half_angle", "soc_sign", "kinetic_factor"):
+    MUTANTS["golden_" + _name] = MUTANTS[_name]
+    PIN_FILES["golden_" + _name] = "tests/test_oracle_golden.py"
 
 
 @pytest.mark.slow
