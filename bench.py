@@ -42,6 +42,7 @@ DEFAULT_INSTANCES = 256
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}  # read + write both components, one pass
 PASSES_PER_STEP = 2
 CUFFT_STEPS = 20
+IMAG_STEPS = 100
 
 
 def log(*a):
@@ -663,6 +664,24 @@ def run_fused(args):
     stop.record(stream)
     barrier()
     cufft_value = world * pts * CUFFT_STEPS / (max_over_ranks(start.elapsed_time(stop), dist, "cuda") * 1e-3)
+
+    # imaginary time on the same batch: three passes per step, the
+    # renormalisation placed after the whole step (Sec. 3.2)
+    c.step_imag(t, DT, 3)
+    barrier()
+    start.record(stream)
+    c.step_imag(t, DT, IMAG_STEPS)
+    stop.record(stream)
+    barrier()
+    imag_s = max_over_ranks(start.elapsed_time(stop), dist, "cuda") * 1e-3
+    c.set_timing(True)
+    c.step_imag(t, DT, IMAG_STEPS)
+    kti = c.timing()
+    c.set_timing(False)
+    imag = {"value": world * pts * IMAG_STEPS / imag_s, "unit": "pt-steps/s", "steps": IMAG_STEPS, "dtau": DT,
+            "ms_per_step": imag_s / IMAG_STEPS * 1e3, "bytes_per_pt_step": 3 * BYTES_PER_PT_PASS[dtype],
+            "step_frac": 3 * alg_bytes * IMAG_STEPS / imag_s / 1e9 / peak,
+            "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kti.items()}}
     c.close()
 
     if rank != 0:
@@ -696,6 +715,7 @@ def run_fused(args):
         "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kt.items()},
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
+        "imag_batch": imag,
         "cufft_comparator": {"value": cufft_value, "unit": "pt-steps/s", "steps": CUFFT_STEPS,
                              "what": "same batch and dt, cuFFT 2D C2C transforms + separate R and K kernels "
                                      "(the paper's step structure)",
