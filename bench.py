@@ -749,7 +749,7 @@ def run_fused(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["fused", "reference"], default="fused")
     ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES)
