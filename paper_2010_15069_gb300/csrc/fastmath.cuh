@@ -8,9 +8,13 @@
 //
 // They have no slow path: the reduction is exact for |h| < 2^12 pi/2 (phases
 // of one substep far beyond anything a stable time step produces); beyond that
-// the result loses accuracy gradually but stays finite.  Checked against FP64
-// references: expi2_m1 within 2e-7 relative to |w| for |h| < 3000, expm1_f
-// within 1e-7 relative.
+// the result loses accuracy gradually but stays finite.  Checked on the GPU
+// against FP64 references over dense argument sweeps of every tier
+// (tests/test_fastmath_gpu.py): expi2_m1 within 2.5e-7 relative to |w| for
+// |h| < 3000 (largest seen 2.14e-7, about 3.6 units of FP32 rounding of
+// |w|), expm1_f within 1.5e-7 relative (largest seen 1.15e-7, at x near 17,
+// where 2^k - 1 is not a float), the shear constants within 3e-7 of the
+// exact rotation of a unit vector.
 #pragma once
 #include <cuda_runtime.h>
 
