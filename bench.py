@@ -1,21 +1,28 @@
-"""Benchmark of the fused two-component TSSP step on GB300.
+"""Benchmark of the fused TSSP passes on GB300.
 
-Workload (one "step" = one Strang step S(dt) of Sec. 3.2 over the whole batch):
-B independent instances of the 256 x 256 real-time problem (box [-10,10]^2,
-harmonic trap, Raman coupling Omega = 2, detuning delta = 0.5 y, kL = 1,
-g11 = g22 = g12 = 200, dt = 5e-4, complex64), each started from the ground
-state of the 64 x 64 two-component problem (g = 100/100/95) upsampled
-spectrally to 256^2 with seeded phase noise per instance.  With B = 256 the
-batch is 256 MiB, twice the L2 size, so every timed step streams from HBM
-(no L2 flush needed).
+Headline workload (one "step" = one imaginary-time step of Sec. 3.2, S(dtau)
+and the renormalisation, over the whole batch): the parameter-sweep batch of
+64 instances at 256^2, 16 at 512^2 and 4 at 1024^2 (12.58 M grid points per
+component, 201 MB of complex64 spinor: above the L2 size, so every step
+streams from HBM and no flush is needed), box [-12, 12]^2, harmonic trap,
+kL = 1, per-instance g (log-uniform in [50, 2000]), g12 / g (in [0.8, 1.2]),
+Omega (in [0, 6]) and detuning gradient (in [0, 1]) from the sweep generator
+(seed 3), vortex-seeded spinors (20 vortices), dtau = 5e-3, complex64
+operators with FP64 reductions and the lagged renormalisation (two passes
+over psi per step), run as one multi-size batch whose size classes share the
+GPU.  The K timed steps run in one call.
 
 Prints one JSON line: grid-point-steps/s (points of one component x steps x
 instances, the paper's N of Sec. 5), the roofline of the dominant kernel, the
+same workload with the exact renormalisation and in complex128, the
 end-to-end figure through the C ABI with host buffers, the CPU oracle timed on
-the host cores, and the SM clocks sampled during the timed region.
+the host cores, the GPU's measured ceilings and the SM clocks sampled during
+the timed region; further objects cover the real-time batch of the 256^2
+problem, the cuFFT comparator, time to residual 1e-8, single large instances
+and the warm-start network.
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead
-(one instance per step, a bounded sample).
+(one 256^2 instance of the sweep per step, a bounded sample).
 """
 from __future__ import annotations
 
@@ -36,13 +43,19 @@ if ROOT not in sys.path:
 
 from paper_2010_15069_gb300 import inputs  # noqa: E402
 
+# real-time batch of the 256^2 problem (Omega = 2, delta = 0.5 y, kL = 1, g = 200)
 NX = NY = 256
 DT = 5e-4
 DEFAULT_INSTANCES = 256
 BYTES_PER_PT_PASS = {"c64": 32, "c128": 64}  # read + write both components, one pass
 PASSES_PER_STEP = 2
 CUFFT_STEPS = 20
-IMAG_STEPS = 100
+
+# imaginary-time sweep batch (the headline)
+SWEEP_CLASSES = [(256, 64), (512, 16), (1024, 4)]   # (grid, instances): 12.58 M points per component
+SWEEP_BOX, SWEEP_DTAU, SWEEP_KL = 12.0, 5e-3, 1.0
+C128_STEPS = 40
+TIMING_STEPS = 200
 
 
 def log(*a):
@@ -162,140 +175,222 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
-# ------------------------------------------------------- time to residual
+# ------------------------------------------------------- sweep batch
 
-TTR_GRID, TTR_BOX, TTR_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK = 256, 12.0, 5e-3, 1e-8, 60000, 250
-
-
-def ttr_problems(B):
-    """B instances of the parameter sweep (g log-uniform in [50, 2000], g12/g in
-    [0.8, 1.2], Omega in [0, 6], detuning gradient in [0, 1], kL = 1, seed 3) on
-    256^2 over [-12, 12]^2, each from a vortex-seeded spinor (20 vortices)."""
-    n, L = TTR_GRID, TTR_BOX
-    prm = inputs.sweep_params(B, seed=3)
-    probs = [inputs.problem(n, n, L, L, Omega=q["Omega"], delta_slope=q["delta_slope"], g11=q["g"], g22=q["g"],
-                            g12=q["g12"], kL=1.0) for q in prm]
-    psi0 = np.stack([inputs.vortex_spinor(probs[0].grid, n_vortices=20, radius=5.0, seed=300 + i)
-                     for i in range(B)])
-    return probs, psi0
-
-
-def time_to_residual(B):
-    """Wall time until every instance has residual <= 1e-8, has stalled (its
-    best residual not halved in 40 checks) or has used its step budget: the
-    plain FP64 path (one complex128 context per instance, one after another)
-    against the batched complex64 -> complex128 ladder (one context for the
-    whole batch, finished instances frozen)."""
-    import torch
-    import paper_2010_15069_gb300 as sp
-    probs, psi0 = ttr_problems(B)
-    n, L = TTR_GRID, TTR_BOX
-
-    def ctx(ninst, idx):
-        c = sp.Context(n, n, L, L, "c128", ninst)
-        for k, i in enumerate(idx):
-            p = probs[i]
-            c.set_potentials_separable(k, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
-        return c
-
-    plain_s, plain_res, plain_steps, plain = 0.0, [], [], []
-    for i in range(B):
-        with ctx(1, [i]) as c:
-            t = torch.from_numpy(psi0[i].copy()).cuda()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res, st = c.relax(t, TTR_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK, give_up=True)
-            plain_s += time.perf_counter() - t0
-            plain_res.append(float(res[0]))
-            plain_steps.append(st[1])
-            plain.append(t.cpu().numpy())
-    with ctx(B, range(B)) as c:
-        t = torch.from_numpy(psi0.copy()).cuda()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res, st = c.relax(t, TTR_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK, ladder=True, give_up=True)
-        ladder_s = time.perf_counter() - t0
-        e_lad = c.energy(t)[:, 0]
-        lad = t.cpu().numpy()
-    with ctx(B, range(B)) as c:
-        e_pl = c.energy(torch.from_numpy(np.stack(plain)).cuda())[:, 0]
-    both = [i for i in range(B) if plain_res[i] <= TTR_TOL and res[i] <= TTR_TOL]
-    return {"workload": f"{B} sweep instances, {n}x{n}, box [-{L:g},{L:g}]^2, kL=1, vortex-seeded, "
-                        f"dtau={TTR_DTAU:g}, check every {TTR_CHECK} steps, at most {TTR_MAX} steps per stage, "
-                        f"instances whose best residual has not halved in 40 checks given up",
-            "tol": TTR_TOL, "plain_fp64_unbatched_s": plain_s, "batched_ladder_s": ladder_s,
-            "speedup": plain_s / ladder_s,
-            "converged": {"plain": sum(r <= TTR_TOL for r in plain_res), "ladder": int((res <= TTR_TOL).sum()),
-                          "of": B},
-            "steps": {"plain_c128_per_instance": plain_steps, "ladder_c64": st[0], "ladder_c128": st[1]},
-            "agreement": {"max_rel_energy_diff": float(np.max(np.abs(e_lad[both] - e_pl[both]) / np.abs(e_pl[both])))
-                          if both else None,
-                          "max_abs_dpsi": float(np.abs(lad[both] - np.stack(plain)[both]).max()) if both else None}}
-
-
-# ------------------------------------------------------- uneven sweep batch
-
-SWEEP_CLASSES = [(256, 64), (512, 16), (1024, 4)]   # (grid, instances): 12.58 M points per component
-SWEEP_BOX, SWEEP_DTAU = 12.0, 5e-3
-
-
-def sweep_throughput(steps=40):
-    """Imaginary-time steps of the uneven sweep batch (64 x 256^2 + 16 x 512^2 +
-    4 x 1024^2, complex64, box [-12, 12]^2, kL = 1, per-instance g, g12, Omega,
-    detuning gradient from the sweep generator) as one multi-size batch (size
-    classes side by side on their own streams) and as three same-size contexts
-    run one after another; grid-point-steps/s of each."""
-    import torch
-    import paper_2010_15069_gb300 as sp
-    total = sum(k for _, k in SWEEP_CLASSES)
-    prm = inputs.sweep_params(total, seed=3)
-    classes = [(n, n, k, SWEEP_BOX, SWEEP_BOX) for n, k in SWEEP_CLASSES]
-    probs, i = [], 0
-    for n, k in SWEEP_CLASSES:
+def sweep_problems(classes=SWEEP_CLASSES, first=0):
+    """(multi-size classes, problems, initial spinors) of the sweep batch: the
+    instances with global indices first .. first + total - 1 (parameters from
+    the sweep generator, seed 3, drawn in that order; spinors with 20 vortices
+    seeded by the global index), grouped by grid size."""
+    total = sum(k for _, k in classes)
+    prm = inputs.sweep_params(first + total, seed=3)[first:]
+    out, probs, psi, i = [], [], [], 0
+    for n, k in classes:
+        out.append((n, n, k, SWEEP_BOX, SWEEP_BOX))
         for _ in range(k):
             q = prm[i]
-            probs.append(inputs.problem(n, n, SWEEP_BOX, SWEEP_BOX, Omega=q["Omega"], delta_slope=q["delta_slope"],
-                                        g11=q["g"], g22=q["g"], g12=q["g12"], kL=1.0))
+            p = inputs.problem(n, n, SWEEP_BOX, SWEEP_BOX, Omega=q["Omega"], delta_slope=q["delta_slope"],
+                               g11=q["g"], g22=q["g"], g12=q["g12"], kL=SWEEP_KL)
+            probs.append(p)
+            psi.append(inputs.vortex_spinor(p.grid, n_vortices=20, radius=5.0, seed=300 + first + i))
             i += 1
-    psi = [inputs.gaussian_spinor(p.grid, width=3.0, seed=40 + j).astype(np.complex64) for j, p in enumerate(probs)]
-    pts = sum(n * n * k for n, k in SWEEP_CLASSES)
-    stream = torch.cuda.Stream()
+    return out, probs, psi
 
-    def timed(run):
-        run(3)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        run(steps)
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) * 1e-3
 
-    with sp.Context.multi(classes, "c64", stream=stream) as c:
-        for j, p in enumerate(probs):
-            c.set_potentials_separable(j, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
-        flat = torch.from_numpy(np.concatenate([x.ravel() for x in psi])).cuda()
-        c.autotune(flat, 5e-4)
-        t_multi = timed(lambda k: c.step_imag(flat, SWEEP_DTAU, k))
-    ctxs, bufs, j = [], [], 0
-    for n, k in SWEEP_CLASSES:
-        cc = sp.Context(n, n, SWEEP_BOX, SWEEP_BOX, "c64", ninst=k, stream=stream)
-        for q in range(k):
-            p = probs[j + q]
-            cc.set_potentials_separable(q, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
-        buf = torch.from_numpy(np.stack(psi[j:j + k])).cuda()
-        cc.autotune(buf, 5e-4)
-        ctxs.append(cc)
-        bufs.append(buf)
+def make_multi(classes, probs, psi, dtype, stream=None):
+    """A multi-size context with every instance's potentials, and the batch
+    as one flat device tensor."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    c = sp.Context.multi(classes, dtype, stream=stream)
+    for j, p in enumerate(probs):
+        c.set_potentials_separable(j, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+    npt = np.complex64 if dtype == "c64" else np.complex128
+    flat = torch.from_numpy(np.concatenate([x.astype(npt).ravel() for x in psi])).cuda()
+    torch.cuda.synchronize()
+    return c, flat
+
+
+def timed_events(stream, run):
+    """Seconds of run() between CUDA events on `stream`, synchronised on both sides."""
+    import torch
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    run()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e-3
+
+
+def kernel_times_in_turn(c, flat, classes, probs, dtype, stream, steps, lagged):
+    """Per-kernel CUDA-event times of `steps` imaginary-time steps of each size
+    class alone on the GPU (a same-size context over the class's part of the
+    batch, the classes one after another on one stream; in the multi-size run
+    the classes' kernels overlap, so a kernel's event-bracketed time there would
+    include the other classes' work).  [(grid, instances, {kind: (launches, ms)})]."""
+    import paper_2010_15069_gb300 as sp
+    out, j = [], 0
+    for (n, _, k, xm, ym), view in zip(classes, c.class_views(flat)):
+        with sp.Context(n, n, xm, ym, dtype, ninst=k, stream=stream) as cc:
+            for q in range(k):
+                p = probs[j + q]
+                cc.set_potentials_separable(q, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+            cc.autotune(view, 5e-4)
+            cc.step_imag(view, SWEEP_DTAU, 3, lagged=lagged)
+            cc.set_timing(True)
+            cc.step_imag(view, SWEEP_DTAU, steps, lagged=lagged)
+            out.append((n, k, cc.timing()))
+            cc.set_timing(False)
         j += k
-    t_seq = timed(lambda k: [cc.step_imag(b, SWEEP_DTAU, k) for cc, b in zip(ctxs, bufs)])
-    for cc in ctxs:
-        cc.close()
-    return {"workload": "64 x 256^2 + 16 x 512^2 + 4 x 1024^2 instances (12.58 M points per component), c64, "
-                        f"imaginary time dtau={SWEEP_DTAU:g}, {steps} steps, sweep parameters (seed 3)",
-            "multi_size_batch_pt_steps_per_s": pts * steps / t_multi,
-            "same_size_contexts_in_turn_pt_steps_per_s": pts * steps / t_seq,
-            "ratio": t_seq / t_multi}
+    return out
+
+
+def dominant(per_class):
+    """(grid, instances, kind, launches, total ms) of the kernel kind with the
+    largest total time among the step's passes."""
+    best = None
+    for n, k, kt in per_class:
+        for kind, (cnt, ms) in kt.items():
+            if kind in ("row_imag_open", "row_imag_rescale"):
+                continue  # once per call, not part of the steady state
+            if best is None or ms > best[4]:
+                best = (n, k, kind, cnt, ms)
+    return best
+
+
+# Algorithmic FP64 flops per grid point (both components) of one pass: each
+# complex transform of length n counts 5 n log2 n (the usual radix-2 count),
+# a row pass runs the inverse and forward x-transforms of both components
+# and the two R(dtau/2) halves (48 flops of pointwise operators), a column
+# pass the forward and inverse y-transforms and K (12 flops).
+def flops_per_point(kind, n):
+    lg = math.log2(n)
+    if kind.startswith("col"):
+        return 2 * 2 * 5 * lg + 12
+    return 2 * 2 * 5 * lg + 48
+
+
+def ceilings():
+    import paper_2010_15069_gb300 as sp
+    try:
+        return sp.spgpe_probe_ceilings()
+    except Exception as e:  # measured ceilings are context; the bench goes on without them
+        return {"error": str(e)}
+
+
+def l2_capacity_mib(ceil):
+    """Largest probed working set whose read bandwidth is still well above the
+    largest set's (HBM) bandwidth: the L2 capacity to within the probe's steps."""
+    tab = ceil.get("read_gbs_by_working_set_mib") if isinstance(ceil, dict) else None
+    if not tab:
+        return None
+    hbm = tab[max(tab)]
+    inside = [m for m, v in tab.items() if v > 1.5 * hbm]
+    return max(inside) if inside else None
+
+
+# ------------------------------------------------------- time to residual
+
+TTR_CLASSES = [(256, 8), (512, 2), (1024, 1)]   # one eighth of the sweep batch
+TTR_TOL, TTR_MAX, TTR_CHECK = 1e-8, 60000, 250
+
+
+def oracle_fixed_point_residual(p, psi, dtau):
+    """The FP64 oracle's discrete-map residual of one exact step from psi: how
+    far psi is from the oracle's own fixed point."""
+    import oracle
+    g = p.grid
+    m = oracle.Model(g.nx, g.ny, g.xmax, g.ymax, V=p.V, delta=p.delta, Omega=p.Omega,
+                     g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+    _, r = m.step(psi, dtau, 1, imag=True, residual=True)
+    return r
+
+
+def time_to_residual():
+    """Wall time until the instances of one eighth of the sweep batch (8 x 256^2
+    + 2 x 512^2 + 1 x 1024^2, the headline's generator) reach residual 1e-8:
+    the plain FP64 path (one complex128 context per instance, one after
+    another, exact renormalisation) against the batched path (one multi-size
+    context: complex64 with the lagged renormalisation down to complex64's
+    rounding floor, then complex128, converged instances frozen).  Both arms
+    give up an instance whose best residual has not halved in 40 checks and
+    have the same step budget per instance (the batched one split evenly over
+    its two stages).  The time is charged over the instances both arms
+    converge: the plain arm's per-instance times summed over them, and a
+    second batched run of exactly those instances.  Per sampled converged
+    instance: the energy and max |dpsi| (up to the global phase) between the
+    two arms and the FP64 oracle's residual of one exact step from the batched
+    result."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    classes, probs, psi = sweep_problems(TTR_CLASSES)
+    B = len(probs)
+    plain = []
+    for p, s in zip(probs, psi):
+        g = p.grid
+        with sp.Context(g.nx, g.ny, g.xmax, g.ymax, "c128") as c:
+            c.set_potentials_separable(0, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+            t = torch.from_numpy(s.copy()).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, st = c.relax(t, SWEEP_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK, give_up=True)
+            el = time.perf_counter() - t0
+            plain.append({"res": float(res[0]), "steps": int(st[1]), "s": el, "psi": t.cpu().numpy(),
+                          "energy": float(c.energy(t)[0, 0])})
+
+    def batched(idx):
+        sub_probs = [probs[i] for i in idx]
+        sub_psi = [psi[i] for i in idx]
+        sub_classes = []
+        for n, _ in TTR_CLASSES:
+            k = sum(1 for p in sub_probs if p.grid.nx == n)
+            if k:
+                sub_classes.append((n, n, k, SWEEP_BOX, SWEEP_BOX))
+        stream = torch.cuda.Stream()
+        c, flat = make_multi(sub_classes, sub_probs, sub_psi, "c128", stream)
+        with c:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, st = c.relax(flat, SWEEP_DTAU, TTR_TOL, TTR_MAX // 2, TTR_CHECK, ladder=True, give_up=True,
+                              lagged=True)
+            el = time.perf_counter() - t0
+            en = c.energy(flat)[:, 0]
+            views = [v.cpu().numpy() for v in c.class_views(flat)]
+        states = [v[j] for v in views for j in range(v.shape[0])]
+        return {"s": el, "res": res, "steps": st, "energy": en, "psi": states}
+
+    full = batched(list(range(B)))
+    both = [i for i in range(B) if plain[i]["res"] <= TTR_TOL and full["res"][i] <= TTR_TOL]
+    sub = full if len(both) == B else (batched(both) if both else None)
+    plain_s = sum(plain[i]["s"] for i in both)
+    checks = []
+    for cls_n in sorted({probs[i].grid.nx for i in both}):
+        i = next(j for j in both if probs[j].grid.nx == cls_n)
+        a, b = plain[i]["psi"], full["psi"][i]
+        ph = np.vdot(b, a)
+        ph = ph / abs(ph) if abs(ph) > 0 else 1.0
+        checks.append({"instance": i, "grid": cls_n,
+                       "rel_energy_diff": abs(full["energy"][i] - plain[i]["energy"]) / abs(plain[i]["energy"]),
+                       "max_abs_dpsi_up_to_phase": float(np.abs(a - b * ph).max()),
+                       "oracle_one_step_residual": oracle_fixed_point_residual(probs[i], b, SWEEP_DTAU)})
+    return {"workload": "8 x 256^2 + 2 x 512^2 + 1 x 1024^2 instances of the sweep generator (seed 3), box "
+                        f"[-12,12]^2, kL=1, 20-vortex seeded, dtau={SWEEP_DTAU:g}, residual checked every "
+                        f"{TTR_CHECK} steps",
+            "tol": TTR_TOL, "step_budget_per_instance": TTR_MAX,
+            "plain": "complex128, one context per instance in turn, exact renormalisation",
+            "batched": "one multi-size context: complex64 (lagged renormalisation) to its rounding floor, "
+                       "then complex128 (lagged), converged instances frozen",
+            "converged": {"plain": sum(pl["res"] <= TTR_TOL for pl in plain),
+                          "batched": int((full["res"] <= TTR_TOL).sum()), "both": len(both), "of": B},
+            "not_converged": {"plain": [i for i in range(B) if plain[i]["res"] > TTR_TOL],
+                              "batched": [i for i in range(B) if full["res"][i] > TTR_TOL]},
+            "plain_fp64_unbatched_s": plain_s, "batched_s": sub["s"] if sub else None,
+            "speedup": plain_s / sub["s"] if sub else None,
+            "plain_steps_per_instance": [pl["steps"] for pl in plain],
+            "batched_steps": {"complex64": int(full["steps"][0]), "complex128": int(full["steps"][1])},
+            "all_instances_s": {"plain": sum(pl["s"] for pl in plain), "batched": full["s"]},
+            "checks": checks}
 
 
 # ------------------------------------------------------- single large instance
@@ -412,21 +507,53 @@ def fno_throughput(n=256, batch=4, steps=10):
 
 # ------------------------------------------------------------- CPU oracle
 
-def oracle_rate(budget_s=12.0, max_steps=400):
-    """The FP64 oracle on one instance of the workload: (pt-steps/s, steps, seconds)."""
+def oracle_instance(i=0):
+    """The FP64 oracle's model and initial spinor of sweep instance i (256^2)."""
     import oracle
-    p = inputs.config1(NX)
-    m = oracle.Model(NX, NY, 10.0, 10.0, V=p.V, delta=p.delta, Omega=p.Omega,
+    _, probs, psi = sweep_problems([(256, i + 1)])
+    p = probs[i]
+    g = p.grid
+    m = oracle.Model(g.nx, g.ny, g.xmax, g.ymax, V=p.V, delta=p.delta, Omega=p.Omega,
                      g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
-    psi = inputs.gaussian_spinor(p.grid, seed=0)
+    return m, psi[i], g.nx * g.ny
+
+
+def oracle_rate(budget_s=12.0, max_steps=2000):
+    """The FP64 oracle on the first 256^2 instance of the sweep (imaginary time,
+    exact renormalisation, one thread): (pt-steps/s, steps, seconds)."""
+    m, psi, npt = oracle_instance(0)
     t0 = time.perf_counter()
-    psi = m.step(psi, DT, 1)
+    psi = m.step(psi, SWEEP_DTAU, 1, imag=True)
     one = time.perf_counter() - t0
     n = int(max(1, min(max_steps, budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
-    m.step(psi, DT, n)
+    m.step(psi, SWEEP_DTAU, n, imag=True)
     dt = time.perf_counter() - t0
-    return NX * NY * n / dt, n, dt
+    return npt * n / dt, n, dt
+
+
+def _oracle_worker(i, budget_s):
+    """One pool worker: oracle imaginary-time steps on sweep instance i for about budget_s."""
+    m, psi, npt = oracle_instance(i)
+    psi = m.step(psi, SWEEP_DTAU, 1, imag=True)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        psi = m.step(psi, SWEEP_DTAU, 10, imag=True)
+        n += 10
+    return npt * n, time.perf_counter() - t0
+
+
+def oracle_rate_all_cores(budget_s=8.0):
+    """The same oracle, one independent 256^2 sweep instance per host core in a
+    spawned process pool (the oracle itself is single-threaded and unchanged):
+    (aggregate pt-steps/s, workers, seconds)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_worker, [(i, budget_s) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    return sum(r[0] / r[1] for r in res), cores, wall
 
 
 def copy_ceiling(t, reps=5):
@@ -461,33 +588,6 @@ def copy_ceiling(t, reps=5):
     t_both = timed(lambda: (h2d(), d2h()))
     return {"h2d_gbs": nbytes / t_in / 1e9, "d2h_gbs": nbytes / t_out / 1e9,
             "both_directions_gbs": 2 * nbytes / t_both / 1e9, "bytes": nbytes}
-
-
-def _oracle_worker(seed, budget_s):
-    """One pool worker: oracle steps on its own instance for about budget_s."""
-    import oracle
-    p = inputs.config1(NX)
-    m = oracle.Model(NX, NY, 10.0, 10.0, V=p.V, delta=p.delta, Omega=p.Omega,
-                     g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
-    psi = m.step(inputs.gaussian_spinor(p.grid, seed=seed), DT, 1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        psi = m.step(psi, DT, 10)
-        n += 10
-    return NX * NY * n, time.perf_counter() - t0
-
-
-def oracle_rate_all_cores(budget_s=8.0):
-    """The same oracle, one independent instance per host core in a spawned
-    process pool (the oracle itself is single-threaded and unchanged):
-    (aggregate pt-steps/s, workers, seconds)."""
-    import multiprocessing as mp
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(cores) as pool:
-        res = pool.starmap(_oracle_worker, [(i, budget_s) for i in range(cores)])
-    wall = time.perf_counter() - t0
-    return sum(r[0] / r[1] for r in res), cores, wall
 
 
 KERNEL_SOURCES = ["fft_core.cuh", "kernels.cuh", "kernels_persist.cuh", "fastmath.cuh", "async_copy.cuh",
@@ -544,44 +644,100 @@ def peaks():
 
 # ------------------------------------------------------------------ arms
 
+def sweep_config(dtype, choice=None, tune_ms=None, chosen_by="auto", renorm="lagged"):
+    cls = [{"grid": [n, n], "instances": k} for n, k in SWEEP_CLASSES]
+    out = {"workload": "imaginary-time parameter-sweep batch 64 x 256^2 + 16 x 512^2 + 4 x 1024^2 (12.58 M points "
+                       f"per component), box [-12,12]^2, kL=1, sweep generator (seed 3), 20-vortex seeded, "
+                       f"dtau={SWEEP_DTAU:g}, {dtype}, {renorm} renormalisation",
+           "classes": cls, "dtau": SWEEP_DTAU, "box": [-SWEEP_BOX, SWEEP_BOX],
+           "l2": "batch larger than L2 (no flush)", "parallelism": "instances sharded per GPU (one batch per GPU)"}
+    if choice is not None:
+        names = ["plain", "persistent TMA", "warp-local TMA"]
+        out["schedule"] = {"per_class": [{"grid": n, "persistent_row": bool(v & 1), "column_pass": names[int(v) >> 1]}
+                                         for (n, _), v in zip(SWEEP_CLASSES, choice)],
+                           "chosen_by": chosen_by,
+                           "autotune_ms_per_step": [float(x) for x in tune_ms] if tune_ms is not None else None}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-    p = inputs.config1(NX)
-    m = oracle.Model(NX, NY, 10.0, 10.0, V=p.V, delta=p.delta, Omega=p.Omega,
-                     g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
-    psi = inputs.gaussian_spinor(p.grid, seed=0)
-    psi = m.step(psi, DT, args.warmup)
+    m, psi, npt = oracle_instance(0)
+    psi = m.step(psi, SWEEP_DTAU, args.warmup, imag=True)
     t0 = time.perf_counter()
-    m.step(psi, DT, args.steps)
+    m.step(psi, SWEEP_DTAU, args.steps, imag=True)
     el = time.perf_counter() - t0
-    value = NX * NY * args.steps / el
+    value = npt * args.steps / el
     line = {
         "impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "pt-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.instances, args.dtype),
+        "config": sweep_config("f64 (oracle)", renorm="exact"),
         "cpu_baseline": {"value": value, "unit": "pt-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one 256x256 instance of the batch, {args.steps} Strang steps"},
+                         "sample": f"the first 256x256 instance of the sweep batch, {args.steps} FP64 imaginary-time "
+                                   "steps (exact renormalisation), one thread"},
         "e2e": {"value": value, "unit": "pt-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def workload_config(B, dtype):
-    return {"workload": f"256x256 real-time two-component GPE x {B} instances (Omega=2, delta=0.5y, kL=1, "
-                        f"g=200, dt=5e-4), {dtype}",
-            "grid": [NX, NY], "instances": B, "dt": DT, "box": [-10.0, 10.0],
-            "l2": "batch larger than L2 (no flush)" if B * NX * NY * 16 > 129e6 else "L2-resident batch",
-            "parallelism": "instances sharded per GPU"}
+def realtime_batch(args, stream, dist, world, rank, peak, peak_kind):
+    """The real-time batch of the 256^2 problem (256 instances, complex64): K
+    steps in one call, the roofline of its dominant pass, and the cuFFT
+    comparator (the paper's step structure) on the same batch."""
+    import torch
+    B, dtype = args.instances, "c64"
+    first, _ = instance_range(rank, world, B)
+    c, t, _ = make_workload(B, dtype, stream=stream, first=first)
+    pts = B * NX * NY
+    if args.schedule == "auto":
+        choice, _ = c.autotune(t, DT)
+    else:
+        choice = np.array([{"persistent": 3, "warp": 5, "plain": 0}[args.schedule]])
+    c.step_real(t, DT, args.warmup)
+    steps = args.steps
+    if dist is not None:
+        dist.barrier()
+    sec = max_over_ranks(timed_events(stream, lambda: c.step_real(t, DT, steps)), dist, "cuda")
+    c.set_timing(True)
+    c.step_real(t, DT, steps)
+    kt = c.timing()
+    c.set_timing(False)
+    kinds = {k: v for k, v in kt.items() if k.startswith(("row_real_fused", "col_real"))}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    n_dom, ms_dom = kinds[dom]
+    avg_s = ms_dom * 1e-3 / n_dom
+    alg_bytes = BYTES_PER_PT_PASS[dtype] * pts
+    achieved = alg_bytes / avg_s / 1e9
+    c.cufft_step_real(t, DT, 3)
+    if dist is not None:
+        dist.barrier()
+    sec_ref = max_over_ranks(timed_events(stream, lambda: c.cufft_step_real(t, DT, CUFFT_STEPS)), dist, "cuda")
+    c.close()
+    value = world * pts * steps / sec
+    return {"workload": f"256x256 real-time two-component GPE x {B} instances (Omega=2, delta=0.5y, kL=1, g=200, "
+                        f"dt=5e-4), c64, each the 64^2 ground state upsampled with seeded phase noise",
+            "value": value, "unit": "pt-steps/s", "steps": steps, "ms_per_step": sec / steps * 1e3,
+            "schedule": {"persistent_row": bool(choice[0] & 1),
+                         "column_pass": ["plain", "persistent TMA", "warp-local TMA"][int(choice[0]) >> 1]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": measured_traffic(f"{dom}:{dtype}:{B}"), "kernel": dom,
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
+                         "peak_source": peak_kind,
+                         "step_frac": PASSES_PER_STEP * alg_bytes * steps / sec / 1e9 / peak},
+            "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kt.items()},
+            "cufft_comparator": {"value": world * pts * CUFFT_STEPS / sec_ref, "unit": "pt-steps/s",
+                                 "steps": CUFFT_STEPS,
+                                 "what": "same batch and dt, cuFFT 2D C2C transforms + separate R and K kernels "
+                                         "(the paper's step structure)",
+                                 "fused_over_cufft": value / (world * pts * CUFFT_STEPS / sec_ref)}}
 
 
 def run_fused(args):
     import torch
-    import paper_2010_15069_gb300 as sp
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -590,99 +746,101 @@ def run_fused(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    B, dtype = args.instances, args.dtype
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        first, _ = instance_range(rank, world, B)
-        c, t, _ = make_workload(B, dtype, stream=stream, first=first)
-    pts = B * NX * NY
+    total = sum(k for _, k in SWEEP_CLASSES)
+    first, _ = instance_range(rank, world, total)
+    classes, probs, psi = sweep_problems(SWEEP_CLASSES, first)
+    pts = sum(n * n * k for n, k in SWEEP_CLASSES)
+    c, flat = make_multi(classes, probs, psi, "c64", stream)
     if args.schedule == "auto":
-        # the library's autotuner picks the pass variants for this batch (scratch copy; psi unchanged)
-        choice, tune_ms = c.autotune(t, DT)
+        # the library's autotuner picks the pass variants per size class (scratch copy; psi unchanged)
+        choice, tune_ms = c.autotune(flat, 5e-4)
     else:
-        # a fixed schedule (e.g. for a profiler run, under which the tuner's timings mean nothing);
-        # set through the environment variable the context reads when it is created
-        choice, tune_ms = np.array([{"persistent": 3, "warp": 5, "plain": 0}[args.schedule]]), None
+        code = {"persistent": 3, "warp": 5, "plain": 0}[args.schedule]
+        choice, tune_ms = np.array([code] * len(SWEEP_CLASSES)), None
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up
-    c.step_real(t, DT, args.warmup)
+    # warm-up, then the timed region: K steps in one call
+    c.step_imag(flat, SWEEP_DTAU, args.warmup, lagged=True)
     barrier()
-    # timed region: K steps in one call (the steady-state cost of a long run)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier()
         start.record(stream)
-        c.step_real(t, DT, args.steps)
+        c.step_imag(flat, SWEEP_DTAU, args.steps, lagged=True)
         stop.record(stream)
         launches = c.last_launches()
         barrier()
     ms = max_over_ranks(start.elapsed_time(stop), dist, "cuda")
     value = world * pts * args.steps / (ms * 1e-3)
-
-    # per-kernel event timing over a second run of the same timed region
-    c.set_timing(True)
-    c.step_real(t, DT, args.steps)
-    kt = c.timing()
-    c.set_timing(False)
-    kinds = {k: v for k, v in kt.items() if k.startswith(("row_real_fused", "col_real"))}
-    dom = max(kinds, key=lambda k: kinds[k][1])
-    n_dom, ms_dom = kinds[dom]
-    avg_s = ms_dom * 1e-3 / n_dom
-    alg_bytes = BYTES_PER_PT_PASS[dtype] * pts
     peak, peak_kind = peaks()
-    achieved = alg_bytes / avg_s / 1e9
-    traffic = measured_traffic(f"{dom}:{dtype}:{B}")
+    psi_bytes = flat.numel() * flat.element_size()
 
-    # end to end through the C ABI with pinned host buffers: H2D, one step, D2H
-    host = torch.empty(tuple(t.shape), dtype=t.dtype, pin_memory=True)
-    host.copy_(t)
+    # per-kernel event times, each size class alone (see kernel_times_in_turn)
+    tsteps = min(args.steps, TIMING_STEPS)
+    per = kernel_times_in_turn(c, flat, classes, probs, "c64", stream, tsteps, True)
+    n_dom, k_dom, kind, cnt, ms_dom = dominant(per)
+    avg_s = ms_dom * 1e-3 / cnt
+    alg_bytes = BYTES_PER_PT_PASS["c64"] * n_dom * n_dom * k_dom
+    achieved = alg_bytes / avg_s / 1e9
+
+    # the exact renormalisation (three passes per step) on the same batch
+    c.step_imag(flat, SWEEP_DTAU, 3)
+    barrier()
+    sec_exact = max_over_ranks(timed_events(stream, lambda: c.step_imag(flat, SWEEP_DTAU, tsteps)), dist, "cuda")
+
+    # end to end through the C ABI with pinned host buffers: every step copies
+    # the batch in, steps it once and copies it back
+    host = torch.empty(tuple(flat.shape), dtype=flat.dtype, pin_memory=True)
+    host.copy_(flat)
     hnp = host.numpy()
-    c.step_real(hnp, DT, 1)
+    c.step_imag(hnp, SWEEP_DTAU, 1)
     e2e_steps = max(3, min(args.steps, 20))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        c.step_real(hnp, DT, 1)
-    e2e_s = time.perf_counter() - t0
+        c.step_imag(hnp, SWEEP_DTAU, 1)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     barrier()
-    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
-    e2e_value = world * pts * e2e_steps / e2e_s
-    psi_bytes = t.numel() * t.element_size()
-    ceiling = copy_ceiling(t)
-
-    # the paper's step structure on the same batch: cuFFT 2D transforms and
-    # separate elementwise kernels (a library comparator, not the product path)
-    c.cufft_step_real(t, DT, 3)
-    barrier()
-    start.record(stream)
-    c.cufft_step_real(t, DT, CUFFT_STEPS)
-    stop.record(stream)
-    barrier()
-    cufft_value = world * pts * CUFFT_STEPS / (max_over_ranks(start.elapsed_time(stop), dist, "cuda") * 1e-3)
-
-    # imaginary time on the same batch: three passes per step, the
-    # renormalisation placed after the whole step (Sec. 3.2)
-    c.step_imag(t, DT, 3)
-    barrier()
-    start.record(stream)
-    c.step_imag(t, DT, IMAG_STEPS)
-    stop.record(stream)
-    barrier()
-    imag_s = max_over_ranks(start.elapsed_time(stop), dist, "cuda") * 1e-3
-    c.set_timing(True)
-    c.step_imag(t, DT, IMAG_STEPS)
-    kti = c.timing()
-    c.set_timing(False)
-    imag = {"value": world * pts * IMAG_STEPS / imag_s, "unit": "pt-steps/s", "steps": IMAG_STEPS, "dtau": DT,
-            "ms_per_step": imag_s / IMAG_STEPS * 1e3, "bytes_per_pt_step": 3 * BYTES_PER_PT_PASS[dtype],
-            "step_frac": 3 * alg_bytes * IMAG_STEPS / imag_s / 1e9 / peak,
-            "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kti.items()}}
+    ceiling = copy_ceiling(flat)
     c.close()
+    del flat, host
+
+    ceil = ceilings() if world == 1 else None
+    fp64_peak = ceil.get("fp64_fma_tflops") if isinstance(ceil, dict) else None
+
+    # the same workload in complex128 (FP64 operators): its own roofline
+    c2, flat2 = make_multi(classes, probs, psi, "c128", stream)
+    c2.autotune(flat2, 5e-4)
+    c2.step_imag(flat2, SWEEP_DTAU, 3, lagged=True)
+    barrier()
+    k128 = min(args.steps, C128_STEPS)
+    sec128 = max_over_ranks(timed_events(stream, lambda: c2.step_imag(flat2, SWEEP_DTAU, k128, lagged=True)), dist,
+                            "cuda")
+    per128 = kernel_times_in_turn(c2, flat2, classes, probs, "c128", stream, k128, True)
+    c2.close()
+    del flat2
+    n8, k8, kind8, cnt8, ms8 = dominant(per128)
+    avg8 = ms8 * 1e-3 / cnt8
+    flops8 = flops_per_point(kind8, n8) * n8 * n8 * k8
+    bytes8 = BYTES_PER_PT_PASS["c128"] * n8 * n8 * k8
+    c128 = {"value": world * pts * k128 / sec128, "unit": "pt-steps/s", "steps": k128,
+            "ms_per_step": sec128 / k128 * 1e3, "dtype": "f64", "renormalisation": "lagged",
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "kernel": f"{kind8} {n8}^2 x {k8}",
+                         "achieved": flops8 / avg8 / 1e12, "peak": fp64_peak,
+                         "frac": flops8 / avg8 / 1e12 / fp64_peak if fp64_peak else None,
+                         "algorithmic_flops_per_launch": flops8, "avg_launch_ms": avg8 * 1e3,
+                         "peak_source": "measured: FP64 fma microbenchmark (spgpe_probe_ceilings)",
+                         "hbm_frac": bytes8 / avg8 / 1e9 / peak},
+            "kernel_ms_by_class": [{"grid": n, "instances": k, "kernels": {kk: {"launches": v[0], "avg_ms": v[1] / v[0]}
+                                                                            for kk, v in kt.items()}}
+                                   for n, k, kt in per128]}
+
+    rt = realtime_batch(args, stream, dist, world, rank, peak, peak_kind) if args.realtime else None
 
     if rank != 0:
         if dist is not None:
@@ -692,53 +850,55 @@ def run_fused(args):
     if world == 1:
         rate, n, el = oracle_rate()
         cpu = {"value": rate, "unit": "pt-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"one 256x256 instance, {n} FP64 Strang steps in {el:.1f} s (single thread)"}
+               "sample": f"the first 256x256 instance of the sweep batch, {n} FP64 imaginary-time steps in "
+                         f"{el:.1f} s (exact renormalisation, one thread)"}
         rate, cores, el = oracle_rate_all_cores()
         cpu_all = {"value": rate, "unit": "pt-steps/s", "cores": cores, "kind": "oracle",
-                   "sample": f"one 256x256 instance per core, FP64 Strang steps for about 8 s each "
+                   "sample": f"one 256x256 sweep instance per core, FP64 imaginary-time steps for about 8 s each "
                              f"({el:.1f} s wall), spawned process pool"}
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "pt-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
-        "config": dict(workload_config(B, dtype),
-                       schedule={"persistent_row": bool(choice[0] & 1),
-                                 "column_pass": ["plain", "persistent TMA", "warp-local TMA"][int(choice[0]) >> 1],
-                                 "chosen_by": args.schedule,
-                                 "autotune_ms_per_step": float(tune_ms[0]) if tune_ms is not None else None}),
+        "dtype": "f32", "data": "synthetic",
+        "config": sweep_config("c64", choice, tune_ms, args.schedule),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                     "frac": achieved / peak, "traffic": measured_traffic(f"{kind}:c64:{n_dom}x{k_dom}"),
+                     "kernel": f"{kind} {n_dom}^2 x {k_dom}",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1e3,
                      "peak_source": peak_kind,
-                     "step_frac": (PASSES_PER_STEP * alg_bytes * args.steps / (ms * 1e-3) / 1e9) / peak},
-        "kernel_ms": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kt.items()},
+                     "kernel_timing": f"{tsteps} steps of each size class alone on the GPU (classes in turn)",
+                     "step_frac": 64 * pts * args.steps / (ms * 1e-3) / 1e9 / peak},
+        "kernel_ms_by_class": [{"grid": n, "instances": k, "kernels": {kk: {"launches": v[0], "avg_ms": v[1] / v[0]}
+                                                                        for kk, v in kt.items()}}
+                               for n, k, kt in per],
+        "exact_renormalisation": {"value": world * pts * tsteps / sec_exact, "unit": "pt-steps/s", "steps": tsteps,
+                                  "ms_per_step": sec_exact / tsteps * 1e3, "bytes_per_pt_step": 96,
+                                  "step_frac": 96 * pts * tsteps / sec_exact / 1e9 / peak},
+        "c128": c128,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
-        "imag_batch": imag,
-        "cufft_comparator": {"value": cufft_value, "unit": "pt-steps/s", "steps": CUFFT_STEPS,
-                             "what": "same batch and dt, cuFFT 2D C2C transforms + separate R and K kernels "
-                                     "(the paper's step structure)",
-                             "fused_over_cufft": value / cufft_value},
-        "e2e": {"value": e2e_value, "unit": "pt-steps/s", "h2d_bytes_per_step": psi_bytes,
+        "e2e": {"value": world * pts * e2e_steps / e2e_s, "unit": "pt-steps/s", "h2d_bytes_per_step": psi_bytes,
                 "d2h_bytes_per_step": psi_bytes, "steps": e2e_steps,
+                "what": "spgpe_step_imag on pinned host buffers, one step per call (exact renormalisation)",
                 "copy_gbs": 2 * psi_bytes * e2e_steps / e2e_s / 1e9, "copy_ceiling": ceiling,
                 "frac_of_copy_ceiling": 2 * psi_bytes * e2e_steps / e2e_s / 1e9 / ceiling["both_directions_gbs"]},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "ceilings": dict(ceil, l2_capacity_mib_estimate=l2_capacity_mib(ceil)) if isinstance(ceil, dict) else ceil,
     }
-    if world == 1 and args.ttr_instances > 0:
-        line["time_to_residual"] = time_to_residual(args.ttr_instances)
+    if rt is not None:
+        line["realtime_batch"] = rt
+    if world == 1 and args.ttr:
+        line["time_to_residual"] = time_to_residual()
     if world == 1 and args.single:
         line["single_instance"] = single_instance(args.single_steps, tune=args.schedule == "auto")
-    if world == 1 and args.sweep:
-        line["uneven_sweep"] = sweep_throughput()
     if world == 1 and args.fno:
         fn = fno_throughput()
         sm = line["clocks"].get("sm_mhz") or 2070.0
         # FP32 FMA peak of the CUDA cores: SMs x 128 lanes x 2 flop x clock
-        peak = torch_sm_count() * 128 * 2 * sm * 1e6 / 1e12
-        fn.update(peak_tflops=peak, frac=fn["achieved_tflops"] / peak,
+        fpk = torch_sm_count() * 128 * 2 * sm * 1e6 / 1e12
+        fn.update(peak_tflops=fpk, frac=fn["achieved_tflops"] / fpk,
                   peak_source="derived: SMs x 128 FP32 lanes x 2 x sampled SM clock")
         line["warm_start_fno"] = fn
     print(json.dumps(line), flush=True)
@@ -752,17 +912,16 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["fused", "reference"], default="fused")
-    ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES)
-    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--instances", type=int, default=DEFAULT_INSTANCES,
+                    help="instances of the real-time 256^2 batch")
     ap.add_argument("--schedule", choices=["auto", "persistent", "warp", "plain"], default="auto",
                     help="pass variants: autotuned (default) or fixed")
-    ap.add_argument("--sweep", type=int, default=1, help="1: also time the uneven sweep batch (0: skip)")
+    ap.add_argument("--realtime", type=int, default=1, help="1: also time the real-time 256^2 batch (0: skip)")
     ap.add_argument("--single", type=int, default=1,
                     help="1: also time one 2048^2 and one 4096^2 instance against the cuFFT comparator (0: skip)")
     ap.add_argument("--single-steps", type=int, default=200, help="timed steps of each single-instance run")
     ap.add_argument("--fno", type=int, default=1, help="1: also time training of the warm-start FNO (0: skip)")
-    ap.add_argument("--ttr-instances", type=int, default=8,
-                    help="sweep instances of the time-to-residual comparison (0: skip it)")
+    ap.add_argument("--ttr", type=int, default=1, help="1: also run the time-to-residual comparison (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

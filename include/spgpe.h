@@ -47,6 +47,9 @@ extern "C" {
 
 enum { SPGPE_C64 = 1, SPGPE_C128 = 2 };
 enum { SPGPE_NORM_TOTAL = 0, SPGPE_NORM_PER_COMPONENT = 1 };
+/* Or'ed into the norm_mode of spgpe_step_imag: the lagged renormalisation
+ * (see there). */
+enum { SPGPE_IMAG_LAGGED = 4 };
 enum {
   SPGPE_OK = 0,
   SPGPE_EINVAL = -1,     /* bad argument: size, pointer, dtype, non-finite input */
@@ -127,6 +130,20 @@ int spgpe_step_real(spgpe_ctx *ctx, void *psi, double dt, int nsteps);
  * components by sqrt((target[0]+target[1]) / (N_up+N_dn)),
  * SPGPE_NORM_PER_COMPONENT scales psi_j by sqrt(target[j] / N_j).  target is a
  * host array of 2 doubles shared by all instances (NULL = {0.5, 0.5}).
+ *
+ * Placement of the rescaling.  By default every step is S(dtau) followed by
+ * the exact rescaling (the definition above; three passes over psi per step).
+ * With SPGPE_IMAG_LAGGED or'ed into norm_mode, the step boundaries after the
+ * first (except the one into the last step when residual_out is given) take
+ * two passes: the opening R(dtau/2) of step n+1 runs on the closing result of
+ * step n scaled by the previous boundary's scale s_{n-1}, and the column pass
+ * that follows multiplies by s_n / s_{n-1}, s_n being the exact scale of step
+ * n.  The linear part of the rescaling is then exact and only the densities
+ * in the opening D(dtau/2) lag: a stationary state of one map is a
+ * stationary state of the other (s_n = s_{n-1} there), so both relax to the
+ * same ground state, while the states of a transient differ at O(dtau g rho
+ * (s_n^2 / s_{n-1}^2 - 1)).  The first boundary and the end of the call are
+ * exact, so the state on return is normalised.
  * residual_out (host, nullable; ninst doubles) receives the discrete-map
  * residual of the last step, ||Psi_{n+1} - Psi_n||_2 / (dtau ||Psi_n||_2)
  * over both components; asking for it synchronises.  A NaN/Inf or zero norm
@@ -159,12 +176,15 @@ int spgpe_step_imag(spgpe_ctx *ctx, void *psi, double dtau, int nsteps, int norm
  *  SPGPE_RELAX_GIVE_UP: also freeze an instance whose smallest residual so
  *   far has not halved in 40 chunks (a metastable state, or a relaxation far
  *   too slow for the budget); its residual stays above tol.
+ *  SPGPE_RELAX_LAGGED: run the chunks with the lagged renormalisation of
+ *   spgpe_step_imag (SPGPE_IMAG_LAGGED); the last step of every chunk stays
+ *   exact, so the residuals compared with tol are those of the exact map.
  * handoff >= 0.  residual_out (host, nullable): ninst doubles, the last
  * residual of each instance.  steps_out (host, nullable): {steps run in
  * complex64 by the ladder, steps run in the context's precision}, counted
  * until the last instance of the stage was done.  Returns SPGPE_OK also when
  * max_steps ran out first (compare residual_out with tol).  Synchronises. */
-enum { SPGPE_RELAX_LADDER = 1, SPGPE_RELAX_GIVE_UP = 2 };
+enum { SPGPE_RELAX_LADDER = 1, SPGPE_RELAX_GIVE_UP = 2, SPGPE_RELAX_LAGGED = 4 };
 int spgpe_relax(spgpe_ctx *ctx, void *psi, double dtau, double tol, int max_steps, int check_every,
                 int norm_mode, const double *target, int flags, double handoff, double *residual_out,
                 int *steps_out);
@@ -297,7 +317,9 @@ const char *spgpe_last_error(const spgpe_ctx *ctx);
 int spgpe_version(void);
 
 /* Introspection for benchmarks: number of kernel launches the last step call
- * issued (real time 2*nsteps + 1, imaginary time 3*nsteps + 1). */
+ * issued (real time 2*nsteps + 1, imaginary time 3*nsteps + 1 with the exact
+ * rescaling, 2*nsteps + 3 with SPGPE_IMAG_LAGGED and nsteps >= 2, both
+ * without residual_out). */
 int spgpe_last_launches(const spgpe_ctx *ctx);
 
 /* Per-kernel timing for benchmarks.  While enabled (enable = 1), every fused
@@ -308,10 +330,29 @@ int spgpe_last_launches(const spgpe_ctx *ctx);
  * 0 real row pass opening, 1 real row pass fused (step end + next start),
  * 2 real row pass closing, 3 real column pass, 4 imaginary row opening,
  * 5 imaginary row pass B (scale + R + FFT), 6 imaginary row pass A (IFFT + R +
- * norm partials), 7 imaginary rescale, 8 imaginary column pass. */
-#define SPGPE_NKINDS 9
+ * norm partials), 7 imaginary rescale, 8 imaginary column pass, 9 imaginary
+ * lagged row pass (IFFT + R + norm partials + predicted scale + R + FFT). */
+#define SPGPE_NKINDS 10
 int spgpe_set_timing(spgpe_ctx *ctx, int enable);
 int spgpe_timing(spgpe_ctx *ctx, double *ms_out, int *count_out);
+
+/* Microbenchmarks of this GPU's ceilings, for reading the measured kernel
+ * times against (no counterpart in the paper; it only launches kernels on a
+ * stream of its own, on the current device, and changes no device setting).
+ * out (host, n_out >= SPGPE_PROBE_COUNT doubles) receives:
+ *  out[0] FP32 fused multiply-add throughput, TFLOP/s (2 flop per fma);
+ *  out[1] FP64 fused multiply-add throughput, TFLOP/s;
+ *  out[2] sincosf throughput, 10^9 calls/s (arguments in [0, 1]);
+ *  out[3] copy bandwidth over 512 MiB + 512 MiB, GB/s (bytes read + written);
+ *  out[4 + k] read bandwidth, GB/s, over a working set of 16, 32, 64, 96, 128,
+ *   160, 192, 256, 512 MiB for k = 0 .. 8, each read repeatedly (about 2 GiB
+ *   per measurement): the drop between sizes marks the L2 capacity.
+ * Each figure is one CUDA-event-timed launch after an untimed one.
+ * Allocates 1 GiB of device memory for the duration of the call and
+ * synchronises.  EINVAL for out NULL or n_out too small; ENOMEM / ECUDA. */
+#define SPGPE_PROBE_NSIZES 9
+#define SPGPE_PROBE_COUNT (4 + SPGPE_PROBE_NSIZES)
+int spgpe_probe_ceilings(double *out, int n_out);
 
 /* Atom numbers of a spinor batch without allocating any memory (the paper has
  * no counterpart: this serves callers that cannot call cudaMalloc, such as

@@ -20,16 +20,17 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SPGPE_RELAX_GIVE_UP,
+from ._lib import (SPGPE_C64, SPGPE_C128, SPGPE_NORM_PER_COMPONENT, SPGPE_NORM_TOTAL, SPGPE_RELAX_GIVE_UP, SPGPE_RELAX_LAGGED, SPGPE_IMAG_LAGGED,
                    SPGPE_RELAX_LADDER, SpgpeError, check, load, SPGPE_OK, SPGPE_ETIMEOUT)
 
 __all__ = [
     "SPGPE_C64", "SPGPE_C128", "SPGPE_OK", "SPGPE_ETIMEOUT", "SPGPE_NORM_TOTAL", "SPGPE_NORM_PER_COMPONENT", "SPGPE_RELAX_LADDER", "SPGPE_RELAX_GIVE_UP",
+    "SPGPE_RELAX_LAGGED", "SPGPE_IMAG_LAGGED",
     "SpgpeError",
     "Context", "FNO", "load",
     "spgpe_init_grid", "spgpe_init_batch", "spgpe_init_multi", "spgpe_set_potentials", "spgpe_set_potentials_separable",
     "spgpe_step_real", "spgpe_step_imag", "spgpe_relax", "spgpe_autotune", "spgpe_observables", "spgpe_add_noise", "spgpe_energy", "spgpe_norm", "spgpe_sync", "spgpe_wait_probe",
-    "spgpe_cufft_step_real", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
+    "spgpe_cufft_step_real", "spgpe_probe_ceilings", "spgpe_destroy", "spgpe_last_error", "spgpe_version",
     "spgpe_last_launches", "spgpe_set_timing", "spgpe_timing",
 ]
 
@@ -160,6 +161,16 @@ def spgpe_wait_probe(ctx, cycles):
 
 def spgpe_cufft_step_real(ctx, psi_ptr, dt, nsteps):
     check(load().spgpe_cufft_step_real(ctx, ctypes.c_void_p(int(psi_ptr)), float(dt), int(nsteps)), ctx)
+
+
+def spgpe_probe_ceilings():
+    """This GPU's measured ceilings (microbenchmarks; see include/spgpe.h)."""
+    from ._lib import PROBE_SIZES_MIB
+    out = np.zeros(4 + len(PROBE_SIZES_MIB))
+    check(load().spgpe_probe_ceilings(_ptr(out), out.size))
+    return {"fp32_fma_tflops": float(out[0]), "fp64_fma_tflops": float(out[1]),
+            "sincosf_gcalls_per_s": float(out[2]), "copy_gbs": float(out[3]),
+            "read_gbs_by_working_set_mib": {int(m): float(v) for m, v in zip(PROBE_SIZES_MIB, out[4:])}}
 
 
 def spgpe_destroy(ctx):
@@ -395,13 +406,16 @@ class Context:
         spgpe_step_real(self._ctx, self._check_psi(psi), dt, nsteps)
         return psi
 
-    def step_imag(self, psi, dtau, nsteps, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5), residual=False):
-        return spgpe_step_imag(self._ctx, self._check_psi(psi), dtau, nsteps, norm_mode, target,
+    def step_imag(self, psi, dtau, nsteps, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5), residual=False,
+                  lagged=False):
+        mode = norm_mode | (SPGPE_IMAG_LAGGED if lagged else 0)
+        return spgpe_step_imag(self._ctx, self._check_psi(psi), dtau, nsteps, mode, target,
                                residual, self.ninst)
 
     def relax(self, psi, dtau, tol, max_steps, check_every=200, norm_mode=SPGPE_NORM_TOTAL, target=(0.5, 0.5),
-              ladder=False, handoff=0.0, give_up=False):
-        flags = (SPGPE_RELAX_LADDER if ladder else 0) | (SPGPE_RELAX_GIVE_UP if give_up else 0)
+              ladder=False, handoff=0.0, give_up=False, lagged=False):
+        flags = ((SPGPE_RELAX_LADDER if ladder else 0) | (SPGPE_RELAX_GIVE_UP if give_up else 0) |
+                 (SPGPE_RELAX_LAGGED if lagged else 0))
         return spgpe_relax(self._ctx, self._check_psi(psi), dtau, tol, max_steps, check_every, norm_mode, target,
                            flags, handoff, self.ninst)
 

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspgpe.so")
 
 SPGPE_C64, SPGPE_C128 = 1, 2
 SPGPE_NORM_TOTAL, SPGPE_NORM_PER_COMPONENT = 0, 1
-SPGPE_RELAX_LADDER, SPGPE_RELAX_GIVE_UP = 1, 2
+SPGPE_IMAG_LAGGED = 4
+SPGPE_RELAX_LADDER, SPGPE_RELAX_GIVE_UP, SPGPE_RELAX_LAGGED = 1, 2, 4
 SPGPE_OK, SPGPE_ETIMEOUT = 0, -5
 STATUS = {0: "SPGPE_OK", -1: "SPGPE_EINVAL", -2: "SPGPE_ENOMEM", -3: "SPGPE_ECUDA",
           -4: "SPGPE_ENONFINITE", -5: "SPGPE_ETIMEOUT", -6: "SPGPE_ESTATE"}
@@ -54,10 +55,12 @@ SIGNATURES = {
     "spgpe_fno_destroy": (None, [_P]),
     "spgpe_fno_last_error": (ctypes.c_char_p, [_P]),
     "spgpe_add_noise": (_I, [_P, _P, _D, ctypes.c_ulonglong]),
+    "spgpe_probe_ceilings": (_I, [_P, _I]),
 }
-NKINDS = 9
+PROBE_SIZES_MIB = [16, 32, 64, 96, 128, 160, 192, 256, 512]
+NKINDS = 10
 KIND_NAMES = ["row_real_open", "row_real_fused", "row_real_close", "col_real", "row_imag_open",
-              "row_imag_B", "row_imag_A", "row_imag_rescale", "col_imag"]
+              "row_imag_B", "row_imag_A", "row_imag_rescale", "col_imag", "row_imag_lagged"]
 
 _lock = threading.Lock()
 _lib = None

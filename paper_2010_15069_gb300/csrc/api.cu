@@ -59,6 +59,7 @@ struct spgpe_ctx {
   size_t n_partials = 0;
   unsigned *d_counters = nullptr;
   double *d_scale = nullptr;
+  double *d_scale2 = nullptr;  // second scale buffer of the lagged renormalisation
   int *d_flags = nullptr;
   int *d_active = nullptr;    // [ninst] per-instance step mask (relaxation freezes converged instances)
   bool use_active = false;
@@ -179,8 +180,8 @@ void free_all(spgpe_ctx *c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   void *ps[] = {c->d_twx, c->d_twy, c->d_twe, c->d_tabx, c->d_taby, c->d_rawx, c->d_rawy, c->d_pot2d, c->d_kxt,
-                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_flags, c->d_active, c->d_scratch,
-                c->d_stage};
+                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_scale2, c->d_flags, c->d_active,
+                c->d_scratch, c->d_stage};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (c->plan_ok) cufftDestroy(c->plan);
@@ -397,6 +398,7 @@ void restrict_row(const spgpe_ctx *c, RowArgs &a, int i0, int ni) {
   a.partials = skip(a.partials, i * c->ny * 2 * sizeof(double));
   a.counters = skip(a.counters, i * sizeof(unsigned));
   a.scale = skip(a.scale, i * 2 * sizeof(double));
+  a.scale_pred = skip(a.scale_pred, i * 2 * sizeof(double));
   a.active = skip(a.active, i * sizeof(int));
   a.ninst = ni;
 }
@@ -405,6 +407,8 @@ void restrict_col(const spgpe_ctx *c, ColArgs &a, int i0, int ni) {
   const size_t es = c->es, i = (size_t)i0;
   a.psi = skip(a.psi, i * 2 * c->plane() * es);
   a.kxt = skip(a.kxt, i * 2 * c->nx * es);
+  a.cnum = skip(a.cnum, i * 2 * sizeof(double));
+  a.cden = skip(a.cden, i * 2 * sizeof(double));
   a.active = skip(a.active, i * sizeof(int));
   a.ninst = ni;
 }
@@ -444,6 +448,7 @@ int kind_of_row(int flags) {
     case kImagFirst: return 4;
     case kImagB: return 5;
     case kImagA: return 6;
+    case kImagLag: return 9;
     default: return 7;
   }
 }
@@ -666,6 +671,7 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
       (r = dev_alloc(c, (void **)&c->d_partials, c->n_partials * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_counters, (size_t)ninst * sizeof(unsigned))) ||
       (r = dev_alloc(c, (void **)&c->d_scale, (size_t)ninst * 2 * sizeof(double))) ||
+      (r = dev_alloc(c, (void **)&c->d_scale2, (size_t)ninst * 2 * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_flags, sizeof(int))) ||
       (r = dev_alloc(c, (void **)&c->d_active, (size_t)ninst * sizeof(int)))) {
     g_init_error = c->err;
@@ -734,8 +740,17 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
 // and without synchronising.  With `residual`, the last step also leaves the
 // residual partials (||Psi_{n+1} - Psi_n||^2, ||Psi_n||^2 per block and
 // instance) in d_partials for imag_collect.
+//
+// Step boundaries (the closing R(dt/2) of step s, the renormalisation, the
+// opening R(dt/2) of step s + 1): exact, two row passes (kImagA ends the step
+// and computes the scale, kImagB applies it and opens the next step); or,
+// with `lagged`, for every boundary but the first and the one before a
+// residual step, one row pass (kImagLag) that opens the next step on the
+// spinor scaled by the previous boundary's scale, with the column pass after
+// it multiplying by the exact scale over that prediction.  The two scale
+// buffers alternate so that a pass never reads the buffer it writes.
 int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, double t0, double t1,
-                 bool residual, int i0 = 0, int ni = -1) {
+                 bool residual, int i0 = 0, int ni = -1, bool lagged = false) {
   int r;
   if ((r = ensure_tables(c, dtau, 1))) return r;
   if (residual && (r = dev_alloc(c, &c->d_scratch, c->psi_bytes()))) return r;
@@ -743,23 +758,52 @@ int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, 
   ra.tgt0 = t0;
   ra.tgt1 = t1;
   ra.norm_mode = norm_mode;
+  ra.scale_pred = c->d_scale2;
   ColArgs ca = col_args(c, p);
+  double *sc[2] = {c->d_scale, c->d_scale2};
   if (ni >= 0) {  // a chunk of instances (host pipeline; no residual)
     restrict_row(c, ra, i0, ni);
     restrict_col(c, ca, i0, ni);
+    sc[0] = ra.scale;
+    sc[1] = const_cast<double *>(ra.scale_pred);
   }
-  for (int s = 1; s <= nsteps; ++s) {
-    if (s == nsteps && residual) {
-      // Keep Psi_n (normalised) for the residual of the last step.
-      if (s > 1) CK(c, row(c, kImagScale, ra));
-      CK(c, cudaMemcpyAsync(c->d_scratch, p, c->psi_bytes(), cudaMemcpyDeviceToDevice, c->st));
-      CK(c, row(c, kImagFirst, ra));
+  // sc[last]: the buffer holding the most recent exact scale
+  int last = 0;
+  if (nsteps == 1 && residual) {
+    // Psi_0 is the input itself
+    CK(c, cudaMemcpyAsync(c->d_scratch, p, c->psi_bytes(), cudaMemcpyDeviceToDevice, c->st));
+  }
+  CK(c, row(c, kImagFirst, ra));
+  CK(c, col(c, true, ca));
+  for (int s = 1; s < nsteps; ++s) {
+    const bool into_residual_step = residual && s == nsteps - 1;
+    if (!lagged || s == 1 || into_residual_step) {
+      ra.scale = sc[0];
+      CK(c, row(c, kImagA, ra));
+      last = 0;
+      if (into_residual_step) {
+        // keep Psi_n (normalised) for the residual of the last step
+        CK(c, row(c, kImagScale, ra));
+        CK(c, cudaMemcpyAsync(c->d_scratch, p, c->psi_bytes(), cudaMemcpyDeviceToDevice, c->st));
+        CK(c, row(c, kImagFirst, ra));
+      } else {
+        CK(c, row(c, kImagB, ra));
+      }
+      CK(c, col(c, true, ca));
     } else {
-      CK(c, row(c, s == 1 ? kImagFirst : kImagB, ra));
+      RowArgs rl = ra;
+      rl.scale_pred = sc[last];
+      rl.scale = sc[last ^ 1];
+      CK(c, row(c, kImagLag, rl));
+      ColArgs cl = ca;
+      cl.cnum = sc[last ^ 1];
+      cl.cden = sc[last];
+      CK(c, col(c, true, cl));
+      last ^= 1;
     }
-    CK(c, col(c, true, ca));
-    CK(c, row(c, kImagA, ra));
   }
+  ra.scale = sc[0];
+  CK(c, row(c, kImagA, ra));
   CK(c, row(c, kImagScale, ra));
   if (residual) {
     ++c->last_launches;
@@ -1073,6 +1117,9 @@ int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
 
 int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_mode, const double *target,
                     double *residual_out) {
+  // SPGPE_IMAG_LAGGED may be or'ed into the normalisation mode
+  const bool lagged = (norm_mode & SPGPE_IMAG_LAGGED) != 0;
+  norm_mode &= ~SPGPE_IMAG_LAGGED;
   if (c && !c->cls.empty()) {
     int r = check_ready(c);
     if (r) return r;
@@ -1090,7 +1137,7 @@ int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_m
     // queue every class before reading any residual, so the classes overlap
     r = for_classes(c, psi, true, [&](spgpe_ctx *k, void *p, int) {
       k->last_launches = 0;
-      return imag_enqueue(k, p, dtau, nsteps, norm_mode, t0, t1, residual_out != nullptr);
+      return imag_enqueue(k, p, dtau, nsteps, norm_mode, t0, t1, residual_out != nullptr, 0, -1, lagged);
     });
     if (r) return r;
     if (residual_out)
@@ -1117,14 +1164,14 @@ int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_m
   }
   if (!residual_out && !is_device_ptr(psi)) {
     r = host_pipeline(c, psi, [&](int i0, int ni, void *p) {
-      return imag_enqueue(c, p, dtau, nsteps, norm_mode, t0, t1, false, i0, ni);
+      return imag_enqueue(c, p, dtau, nsteps, norm_mode, t0, t1, false, i0, ni, lagged);
     });
     return r ? r : read_flags(c);
   }
   void *p;
   bool host;
   if ((r = begin_psi(c, psi, &p, &host))) return r;
-  if ((r = imag_enqueue(c, p, dtau, nsteps, norm_mode, t0, t1, residual_out != nullptr))) return r;
+  if ((r = imag_enqueue(c, p, dtau, nsteps, norm_mode, t0, t1, residual_out != nullptr, 0, -1, lagged))) return r;
   if (residual_out && (r = imag_collect(c, dtau, residual_out))) return r;
   if ((r = end_psi(c, psi, host))) return r;
   if (residual_out || host) return read_flags(c);
@@ -1389,7 +1436,7 @@ struct Member {
 // chunks (a metastable state, or a relaxation far too slow for the budget).
 constexpr int kStallChecks = 40;
 int relax_stage(spgpe_ctx *owner, std::vector<Member> &mem, int ntotal, double dtau, double tol, int max_steps,
-                int check, int norm_mode, double t0, double t1, bool to_floor, bool give_up,
+                int check, int norm_mode, double t0, double t1, bool to_floor, bool give_up, bool lagged,
                 std::vector<double> &res, int *steps, int *launches) {
   const double floor64 = std::ldexp(1.0, -18) / dtau;
   std::vector<int> act((size_t)ntotal, 1), since((size_t)ntotal, 0);
@@ -1425,7 +1472,8 @@ int relax_stage(spgpe_ctx *owner, std::vector<Member> &mem, int ntotal, double d
     if (multi && (rc = fork_classes(owner))) return rc;
     for (Member &m : mem) {
       m.c->last_launches = 0;
-      if ((rc = imag_enqueue(m.c, m.p, dtau, n, norm_mode, t0, t1, true))) return fail(owner, rc, m.c->err);
+      if ((rc = imag_enqueue(m.c, m.p, dtau, n, norm_mode, t0, t1, true, 0, -1, lagged)))
+        return fail(owner, rc, m.c->err);
       graph_launches += m.c->last_launches;
     }
     if (multi && (rc = join_classes(owner))) return rc;
@@ -1538,7 +1586,8 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
   if (!psi || !(dtau > 0) || !std::isfinite(dtau) || !(tol > 0) || max_steps < 1 || check_every < 1 ||
       !(handoff >= 0) || !std::isfinite(handoff))
     return fail(c, SPGPE_EINVAL, "bad psi, dtau, tol, max_steps, check_every or handoff");
-  if (flags & ~(SPGPE_RELAX_LADDER | SPGPE_RELAX_GIVE_UP)) return fail(c, SPGPE_EINVAL, "unknown flags");
+  if (flags & ~(SPGPE_RELAX_LADDER | SPGPE_RELAX_GIVE_UP | SPGPE_RELAX_LAGGED))
+    return fail(c, SPGPE_EINVAL, "unknown flags");
   if (norm_mode != SPGPE_NORM_TOTAL && norm_mode != SPGPE_NORM_PER_COMPONENT)
     return fail(c, SPGPE_EINVAL, "bad norm_mode");
   const double t0 = target ? target[0] : 0.5, t1 = target ? target[1] : 0.5;
@@ -1546,6 +1595,7 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
     return fail(c, SPGPE_EINVAL, "targets must be finite, non-negative, not both zero");
   const bool ladder = (flags & SPGPE_RELAX_LADDER) && c->dtype == SPGPE_C128;
   const bool give_up = (flags & SPGPE_RELAX_GIVE_UP) != 0;
+  const bool lagged = (flags & SPGPE_RELAX_LAGGED) != 0;
   void *p;
   bool host;
   if ((r = begin_psi(c, psi, &p, &host))) return r;
@@ -1569,7 +1619,7 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
     }
     // complex64 down to the hand-off residual, or (handoff = 0) its rounding floor
     r = relax_stage(c, m64, c->ninst, dtau, std::max(tol, handoff), max_steps, check_every, norm_mode, t0, t1,
-                    handoff == 0.0, give_up, res, &s64, &launches);
+                    handoff == 0.0, give_up, lagged, res, &s64, &launches);
     if (r) return r;
     for (Member &m : mem) {
       CK(c, launch_convert(m.c->d_psi64, 8, m.p, 16, (long)m.c->ninst * 2 * m.c->plane(), m.c->sms, m.c->st));
@@ -1577,8 +1627,8 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
     }
   }
   // the context's own precision (a staged host spinor is already on the device)
-  r = relax_stage(c, mem, c->ninst, dtau, tol, max_steps, check_every, norm_mode, t0, t1, false, give_up, res, &s,
-                  &launches);
+  r = relax_stage(c, mem, c->ninst, dtau, tol, max_steps, check_every, norm_mode, t0, t1, false, give_up, lagged,
+                  res, &s, &launches);
   if (r) return r;
   if (!c->cls.empty() && (r = join_classes(c))) return r;
   c->last_launches = launches;

@@ -13,7 +13,8 @@ enum : int {
   F_SCALE = 8,    // multiply by the per-instance scale (imaginary-time renormalisation)
   F_RSTART = 16,  // R(dt/2): the next step's opening half
   F_FFT = 32,     // forward FFT along x, store k_x-space row
-  F_IMAG = 64     // imaginary time: exp(-tau H) factors instead of exp(-i tau H)
+  F_IMAG = 64,    // imaginary time: exp(-tau H) factors instead of exp(-i tau H)
+  F_LAG = 128     // between R_end and R_start: multiply by the predicted scale (lagged renormalisation)
 };
 
 constexpr int kRealFirst = F_RSTART | F_FFT;
@@ -23,6 +24,13 @@ constexpr int kImagFirst = F_IMAG | F_RSTART | F_FFT;
 constexpr int kImagB = F_IMAG | F_SCALE | F_RSTART | F_FFT;
 constexpr int kImagA = F_IMAG | F_IFFT | F_REND | F_PART;
 constexpr int kImagScale = F_IMAG | F_SCALE;
+// Lagged renormalisation (one row pass between steps): the step's closing
+// R(dt/2), the atom-number partials of its result (the last unit writes the
+// exact scale s_n), the scale predicted from the previous step (s_{n-1}), the
+// next step's opening R(dt/2) and the x-FFT; the column pass that follows
+// multiplies by s_n / s_{n-1}, so the linear part of the renormalisation is
+// exact and only the densities seen by the opening D lag behind.
+constexpr int kImagLag = F_IMAG | F_IFFT | F_REND | F_PART | F_LAG | F_RSTART | F_FFT;
 
 // Arguments of the fused row pass (x direction, both components per thread).
 struct RowArgs {
@@ -43,7 +51,8 @@ struct RowArgs {
   int omega_pieces;       // bit 0: some Omega_y != 0, bit 1: some Omega_x != 0 (separable pieces)
   double *partials;       // [ninst][gridDim.x][2]
   unsigned *counters;     // [ninst], zero between launches
-  double *scale;          // [ninst][2]
+  double *scale;          // [ninst][2]: written by the last unit of F_PART, read by F_SCALE
+  const double *scale_pred;  // [ninst][2]: the predicted scale F_LAG applies (never the buffer written)
   double tgt0, tgt1;      // target atom numbers
   int norm_mode;          // 0 total, 1 per component
   double wgt;             // dx * dy
@@ -62,6 +71,10 @@ struct ColArgs {
   const void *kxt;        // [ninst][2][nx] complex a_j(kx) - 1
   const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
   const void *tw;         // twiddle table of the y plan (see TwType in fft_core.cuh)
+  // Lagged renormalisation: each column of instance i, component j is also
+  // multiplied by cnum[2 i + j] / cden[2 i + j] (the exact scale over the
+  // predicted one); null: no such factor.
+  const double *cnum, *cden;
   int nx, ny, ninst, C;
 };
 
@@ -120,6 +133,11 @@ struct LaunchShape {
 // explicitly instantiated in kernels_row.cu and kernels_col.cu.  They return
 // cudaGetLastError() after the launch.
 template <class T> LaunchShape row_shape(int nx, int ny);
+// The row pass of one flag combination (plain / persistent), instantiated per
+// flag group in the kernels_row_*.cu units; launch_row / launch_row_p
+// dispatch on the flags (kernels_row_dispatch.cu).
+template <class T, int F> cudaError_t launch_row_f(RowArgs a, cudaStream_t s);
+template <class T, int F> cudaError_t launch_row_pf(RowArgs a, cudaStream_t s, int sms);
 template <class T> LaunchShape col_shape(int nx, int ny);
 template <class T> cudaError_t launch_row(int flags, RowArgs a, cudaStream_t s);
 template <class T> cudaError_t launch_col(bool imag, ColArgs a, cudaStream_t s);

@@ -314,7 +314,7 @@ template <class T, int C> struct ColAccC {
 template <class T, int N, int F, int TIER>
 __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4<T> *tab, const q4<T> &ty,
                                       const q4<T> *p2, T g11, T g22, T g12, T htau, T xang, int pieces, bool ymerge,
-                                      T tm, T sm, double (&nsum)[2]) {
+                                      T tm, T sm, T su, T sd, T (&nsum)[2]) {
   constexpr bool IMAG = (F & F_IMAG) != 0;
   constexpr bool MERGE = !IMAG && (F & F_REND) && (F & F_RSTART) && !(F & F_PART);
   const q4<T> px = tab[x];
@@ -340,8 +340,12 @@ __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4
       applyX<IMAG>(u, d, xc, pieces);
     }
     if constexpr (F & F_PART) {
-      nsum[0] += double(cabs2(u));
-      nsum[1] += double(cabs2(d));
+      nsum[0] += cabs2(u);
+      nsum[1] += cabs2(d);
+    }
+    if constexpr (F & F_LAG) {
+      u = cscale(u, su);
+      d = cscale(d, sd);
     }
     if constexpr (F & F_RSTART) {
       applyX<IMAG>(u, d, xc, pieces);
@@ -359,24 +363,25 @@ __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4
 template <class T, int LOGN, int LOGE, int F, int TIER>
 __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&pd)[(1 << LOGE) / 2], int t, int comp,
                                          int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T g11, T g22,
-                                         T g12, T htau, T xang, int pieces, bool ymerge, T tm, T sm,
-                                         double (&nsum)[2]) {
+                                         T g12, T htau, T xang, int pieces, bool ymerge, T tm, T sm, T su, T sd,
+                                         T (&nsum)[2]) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
 #pragma unroll
   for (int j = 0; j < H; ++j)
     r_one<T, N, F, TIER>(pu[j], pd[j], t + (j + comp * H) * TT, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces,
-                         ymerge, tm, sm, nsum);
+                         ymerge, tm, sm, su, sd, nsum);
 }
 
 // Row-pass compute on registers already loaded: v holds this thread's
 // component at positions t + m*TT of row y.  tab points at the instance's
-// x step table (global or shared memory).  Returns the FP64 atom-number
-// partials of the R_end result when F has F_PART.
+// x step table (global or shared memory).  Adds this thread's atom-number
+// partials of the R_end result (its H points of both components, summed in
+// the working precision) to nsum when F has F_PART.
 template <class T, int LOGN, int LOGE, int F, class Acc>
 __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int comp, unsigned mask, int half,
                                             int inst, int y, const Acc &acc, const q4<T> *tab,
-                                            const RowArgs &a, double (&nsum)[2]) {
-  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
+                                            const RowArgs &a, T (&nsum)[2]) {
+  constexpr int E = 1 << LOGE, H = E / 2;
   constexpr bool IMAG = (F & F_IMAG) != 0;
   if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 1>(v, t, a.tw, acc);
   if constexpr (F & F_SCALE) {
@@ -394,6 +399,11 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
     const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
     T tm = T(0), sm = T(0);
+    T su = T(1), sd = T(1);
+    if constexpr ((F & F_LAG) != 0) {
+      su = T(a.scale_pred[2 * inst]);
+      sd = T(a.scale_pred[2 * inst + 1]);
+    }
     bool ymerge = false;
     if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
     // One phase tier per warp: the shortest series whose range holds |htau e|
@@ -414,11 +424,15 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
 #pragma unroll
     for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
                                                       d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
+    // (the lagged pass scales the densities between R_end and R_start by the
+    // squared predicted scale)
+    if constexpr ((F & F_LAG) != 0) rmax *= fmax(T(1), fmax(su * su, sd * sd));
     const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
     const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
     const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
 #define SPGPE_R_POINTS(TIER) \
-  r_points<T, LOGN, LOGE, F, TIER>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, nsum)
+  r_points<T, LOGN, LOGE, F, TIER>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, \
+                                   su, sd, nsum)
     if constexpr (sizeof(T) == 8) {
       SPGPE_R_POINTS(2);
     } else {
@@ -442,17 +456,63 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
   if constexpr (F & F_FFT) block_fft<LOGN, LOGE, -1, 1>(v, t, a.tw, acc);
 }
 
-// FP64 atom-number partials of one row group; the last group of the
-// instance to finish reduces them in a fixed order and writes the
+// Sum of a per-thread pair over the block into thread 0: in single
+// precision each warp first adds its lanes' values in a fixed FP32 tree (the
+// summands are non-negative, so the relative error stays below 13 units of
+// FP32 rounding for 8 points per lane), and the warps' totals go on in FP64;
+// double precision sums in FP64 throughout (block_sum).
+template <class T> __device__ __forceinline__ void block_sum_pair(const T (&v)[2], double (&out)[2]) {
+  if constexpr (sizeof(T) == 4) {
+    __shared__ double red2[2][32];
+    float w0 = v[0], w1 = v[1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+      w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+      red2[0][w] = double(w0);
+      red2[1][w] = double(w1);
+    }
+    __syncthreads();
+    out[0] = out[1] = 0.0;
+    if (threadIdx.x == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+      for (int k = 0; k < nw; ++k) {
+        out[0] += red2[0][k];
+        out[1] += red2[1][k];
+      }
+    }
+    __syncthreads();
+  } else {
+    out[0] = v[0];
+    out[1] = v[1];
+    block_sum<2>(out);
+  }
+}
+
+// Count a finished row group: an atomic add with release-acquire ordering at
+// GPU scope, so the group's partial sums written before it are visible to the
+// group that sees the final count (and that group sees every other group's).
+__device__ __forceinline__ unsigned count_group(unsigned *counter) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
+  return old;
+}
+
+// Atom-number partials of one row group; the last group of the instance to
+// finish reduces them in a fixed order (FP64) and writes the
 // renormalisation scale (Sec. 3.2).  Called by every thread of the block.
-__device__ __forceinline__ void row_partials(const RowArgs &a, int inst, int group, int ngroups, double (&nsum)[2]) {
+template <class T>
+__device__ __forceinline__ void row_partials(const RowArgs &a, int inst, int group, int ngroups, const T (&tsum)[2]) {
   __shared__ int s_last;
-  block_sum<2>(nsum);
+  double nsum[2];
+  block_sum_pair<T>(tsum, nsum);
   if (threadIdx.x == 0) {
     a.partials[((long)inst * ngroups + group) * 2] = nsum[0];
     a.partials[((long)inst * ngroups + group) * 2 + 1] = nsum[1];
-    __threadfence();
-    const unsigned prev = atomicAdd(&a.counters[inst], 1u);
+    const unsigned prev = count_group(&a.counters[inst]);
     s_last = (prev == (unsigned)ngroups - 1u);
   }
   __syncthreads();
@@ -501,8 +561,14 @@ template <int TT> __device__ __forceinline__ RowPlace row_place() {
   return r;
 }
 
+// Largest block of the plain row pass: kRowMaxThreads, or the 2*TT threads of
+// one row when that is more (4096-point rows; 2048-point complex128 rows).
+__host__ __device__ constexpr int row_block_max(int logn, int loge) {
+  return 2 * ((1 << logn) >> loge) > kRowMaxThreads ? 2 * ((1 << logn) >> loge) : kRowMaxThreads;
+}
+
 template <class T, int LOGN, int LOGE, int F>
-__global__ void __launch_bounds__(LOGN <= 11 ? kRowMaxThreads : 2 * kRowMaxThreads, sizeof(T) == 4 && LOGN <= 11 ? 3 : 1)
+__global__ void __launch_bounds__(row_block_max(LOGN, LOGE), sizeof(T) == 4 && LOGN <= 11 ? 3 : 1)
 row_pass(const RowArgs a) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -519,15 +585,26 @@ row_pass(const RowArgs a) {
   cx<T> v[1][E];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[0][m] = p[pl.t + m * TT];
-  double nsum[2] = {0.0, 0.0};
+  T nsum[2] = {T(0), T(0)};
   row_compute<T, LOGN, LOGE, F>(v, pl.t, pl.comp, pl.mask, pl.half, inst, y, acc,
                                 reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N, a, nsum);
-  if constexpr (F & F_PART) row_partials(a, inst, blockIdx.x, gridDim.x, nsum);
+  if constexpr (F & F_PART) row_partials<T>(a, inst, blockIdx.x, gridDim.x, nsum);
 #pragma unroll
   for (int m = 0; m < E; ++m) p[pl.t + m * TT] = v[0][m];
 }
 
 // ---------------------------------------------------------- column pass
+
+// The column pass's final factor for column group pc = 2 inst + comp: the
+// inverse transform's 1/(nx ny), times the correction s_n / s_{n-1} of the
+// lagged renormalisation when there is one.
+template <class T> __device__ __forceinline__ T col_inv(const ColArgs &a, int pc) {
+  if constexpr (sizeof(T) == 4) {
+    return a.cnum ? (float)(a.inv_d * (a.cnum[pc] / a.cden[pc])) : a.inv_f;
+  } else {
+    return a.cnum ? a.inv_d * (a.cnum[pc] / a.cden[pc]) : a.inv_d;
+  }
+}
 
 // Column-pass compute on registers already loaded: forward y-FFT, K(dt) with
 // am = a_j(kx) - 1 and bm = b(ky) - 1 (global or shared), inverse y-FFT.
@@ -577,8 +654,7 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
 #pragma unroll
   for (int m = 0; m < E; ++m) v[0][m] = col[t * a.nx + m * rs];
   const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
-  T inv;
-  if constexpr (sizeof(T) == 4) inv = a.inv_f; else inv = a.inv_d;
+  const T inv = col_inv<T>(a, inst * 2 + comp);
   col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, reinterpret_cast<const cx<T> *>(a.kyt), inv);
 #pragma unroll
   for (int m = 0; m < E; ++m) col[t * a.nx + m * rs] = v[0][m];

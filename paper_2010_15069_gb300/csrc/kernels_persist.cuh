@@ -47,24 +47,34 @@ __host__ __device__ constexpr size_t rowu_bytes(int n, int rows, int es) {
   return ((size_t)rows * 2 * n * es + (size_t)rows * row_stride(n, es) * es + 8 + 127) / 128 * 128;
 }
 
-// Atom-number partials of one warp unit (its rows belong to one instance);
-// the last unit of the instance reduces them in a fixed order and writes the
-// renormalisation scale, as row_partials does for blocks.
-__device__ __forceinline__ void warp_partials(const RowArgs &a, int inst, int group, int ngroups,
-                                              double (&nsum)[2]) {
-  const int lane = threadIdx.x & 31;
+// Atom-number partials of one warp unit (its rows belong to one instance),
+// in two halves so that the count's round trip overlaps the unit's stores:
+// warp_partials_post adds the lanes' values in a fixed tree in the working
+// precision (FP32 for complex64: non-negative summands, relative error below
+// 13 units of FP32 rounding for 8 points per lane), lane 0 writes the unit's
+// pair in FP64 and counts the unit (release-acquire), returning the count
+// before it; warp_partials_finish lets the last unit of the instance reduce
+// all pairs in a fixed order (FP64) and write the renormalisation scale, as
+// row_partials does for blocks.
+template <class T>
+__device__ __forceinline__ unsigned warp_partials_post(const RowArgs &a, int inst, int group, int ngroups,
+                                                       T (&tsum)[2]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    nsum[0] += __shfl_xor_sync(0xffffffffu, nsum[0], o);
-    nsum[1] += __shfl_xor_sync(0xffffffffu, nsum[1], o);
+    tsum[0] += __shfl_xor_sync(0xffffffffu, tsum[0], o);
+    tsum[1] += __shfl_xor_sync(0xffffffffu, tsum[1], o);
   }
   unsigned prev = 0;
-  if (lane == 0) {
-    a.partials[((long)inst * ngroups + group) * 2] = nsum[0];
-    a.partials[((long)inst * ngroups + group) * 2 + 1] = nsum[1];
-    __threadfence();
-    prev = atomicAdd(&a.counters[inst], 1u);
+  if ((threadIdx.x & 31) == 0) {
+    a.partials[((long)inst * ngroups + group) * 2] = double(tsum[0]);
+    a.partials[((long)inst * ngroups + group) * 2 + 1] = double(tsum[1]);
+    prev = count_group(&a.counters[inst]);
   }
+  return prev;
+}
+
+__device__ __forceinline__ void warp_partials_finish(const RowArgs &a, int inst, int ngroups, unsigned prev) {
+  const int lane = threadIdx.x & 31;
   prev = __shfl_sync(0xffffffffu, prev, 0);
   if (prev != (unsigned)ngroups - 1u) return;
   __threadfence();
@@ -219,16 +229,18 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
     }
     const int inst = u / upi, group = u - inst * upi;
     const int y = group * RU + lrow;
-    double nsum[2] = {0.0, 0.0};
+    T nsum[2] = {T(0), T(0)};
     row_compute<T, LOGN, LOGE, F>(v, t, comp, 0xffffffffu, 16, inst, y, acc,
                                   reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N, ac, nsum);
+    unsigned prev = 0;
     if constexpr (F & F_PART) {
-      if constexpr (U::WARP) warp_partials(a, inst, group, upi, nsum);
-      else row_partials(a, inst, group, upi, nsum);
+      if constexpr (U::WARP) prev = warp_partials_post<T>(a, inst, group, upi, nsum);
+      else row_partials<T>(a, inst, group, upi, nsum);
     }
     cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N + t;
 #pragma unroll
     for (int m = 0; m < E; ++m) p[m * TT] = v[0][m];
+    if constexpr ((F & F_PART) && U::WARP) warp_partials_finish(a, inst, upi, prev);
     u = un;
   }
 }
@@ -287,8 +299,6 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
   }
   for (int k = threadIdx.x; k < N; k += blockDim.x) btab[k] = reinterpret_cast<const cx<T> *>(a.kyt)[k];
   __syncthreads();
-  T inv;
-  if constexpr (sizeof(T) == 4) inv = a.inv_f; else inv = a.inv_d;
 
   for (int i = 0; tile < ntiles; ++i) {
     const int s = i & 1;
@@ -310,7 +320,7 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[(long)pc * a.nx + kx];
     __syncthreads();  // the dense tile is read; its space now serves the exchanges
     const ColAccC<T, C> acc{b + c};
-    col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, btab, inv);
+    col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, btab, col_inv<T>(a, pc));
     cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + (long)pc * N * a.nx + kx;
     const int rs = TT * a.nx;
 #pragma unroll
@@ -398,7 +408,6 @@ __global__ void __launch_bounds__(256, 2)
   }
   for (int k = threadIdx.x; k < N; k += blockDim.x) btab[k] = reinterpret_cast<const cx<float> *>(a.kyt)[k];
   __syncthreads();
-  const float inv = a.inv_f;
   int refill = ntiles, refill_s = 0;  // a buffer whose store must finish reading before its reload
   for (int i = 0; tile < ntiles; ++i) {
     const int s = i & 1;
@@ -425,7 +434,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int m = 0; m < E; ++m) v[0][m] = *reinterpret_cast<const cx<float> *>(tb + sw_off(t + m * TT, c));
     const cx<float> am = reinterpret_cast<const cx<float> *>(a.kxt)[(long)pc * a.nx + kx];
-    col_compute<float, 8, 4, IMAG>(v, t, acc, a.tw, am, btab, inv);
+    col_compute<float, 8, 4, IMAG>(v, t, acc, a.tw, am, btab, col_inv<float>(a, pc));
     // results in place (this warp's columns only), then one store of the tile
 #pragma unroll
     for (int m = 0; m < E; ++m) *reinterpret_cast<cx<float> *>(tb + sw_off(t + m * TT, c)) = v[0][m];

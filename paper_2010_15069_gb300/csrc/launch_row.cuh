@@ -48,31 +48,20 @@ template <class T, int LOGN, int F> cudaError_t row_launch_n(RowArgs a, cudaStre
   return cudaGetLastError();
 }
 
-template <class T, int LOGN> cudaError_t row_launch_f(int flags, const RowArgs &a, cudaStream_t st) {
-  switch (flags) {
-    case kRealFirst: return row_launch_n<T, LOGN, kRealFirst>(a, st);
-    case kRealMid: return row_launch_n<T, LOGN, kRealMid>(a, st);
-    case kRealLast: return row_launch_n<T, LOGN, kRealLast>(a, st);
-    case kImagFirst: return row_launch_n<T, LOGN, kImagFirst>(a, st);
-    case kImagB: return row_launch_n<T, LOGN, kImagB>(a, st);
-    case kImagA: return row_launch_n<T, LOGN, kImagA>(a, st);
-    case kImagScale: return row_launch_n<T, LOGN, kImagScale>(a, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <class T> cudaError_t launch_row(int flags, RowArgs a, cudaStream_t st) {
+// One flag combination, every row length (instantiated per flag group in
+// the kernels_row_*.cu units so that they compile in parallel).
+template <class T, int F> cudaError_t launch_row_f(RowArgs a, cudaStream_t st) {
   switch (a.nx) {
-    case 8: return row_launch_f<T, 3>(flags, a, st);
-    case 16: return row_launch_f<T, 4>(flags, a, st);
-    case 32: return row_launch_f<T, 5>(flags, a, st);
-    case 64: return row_launch_f<T, 6>(flags, a, st);
-    case 128: return row_launch_f<T, 7>(flags, a, st);
-    case 256: return row_launch_f<T, 8>(flags, a, st);
-    case 512: return row_launch_f<T, 9>(flags, a, st);
-    case 1024: return row_launch_f<T, 10>(flags, a, st);
-    case 2048: return row_launch_f<T, 11>(flags, a, st);
-    case 4096: return row_launch_f<T, 12>(flags, a, st);
+    case 8: return row_launch_n<T, 3, F>(a, st);
+    case 16: return row_launch_n<T, 4, F>(a, st);
+    case 32: return row_launch_n<T, 5, F>(a, st);
+    case 64: return row_launch_n<T, 6, F>(a, st);
+    case 128: return row_launch_n<T, 7, F>(a, st);
+    case 256: return row_launch_n<T, 8, F>(a, st);
+    case 512: return row_launch_n<T, 9, F>(a, st);
+    case 1024: return row_launch_n<T, 10, F>(a, st);
+    case 2048: return row_launch_n<T, 11, F>(a, st);
+    case 4096: return row_launch_n<T, 12, F>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -104,31 +93,18 @@ template <class T, int LOGN, int F> cudaError_t rowp_launch_n(RowArgs a, cudaStr
   return cudaGetLastError();
 }
 
-template <class T, int LOGN> cudaError_t rowp_launch_f(int flags, const RowArgs &a, cudaStream_t st, int sms) {
-  switch (flags) {
-    case kRealFirst: return rowp_launch_n<T, LOGN, kRealFirst>(a, st, sms);
-    case kRealMid: return rowp_launch_n<T, LOGN, kRealMid>(a, st, sms);
-    case kRealLast: return rowp_launch_n<T, LOGN, kRealLast>(a, st, sms);
-    case kImagFirst: return rowp_launch_n<T, LOGN, kImagFirst>(a, st, sms);
-    case kImagB: return rowp_launch_n<T, LOGN, kImagB>(a, st, sms);
-    case kImagA: return rowp_launch_n<T, LOGN, kImagA>(a, st, sms);
-    case kImagScale: return rowp_launch_n<T, LOGN, kImagScale>(a, st, sms);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <class T> cudaError_t launch_row_p(int flags, RowArgs a, cudaStream_t st, int sms) {
+template <class T, int F> cudaError_t launch_row_pf(RowArgs a, cudaStream_t st, int sms) {
   switch (a.nx) {
-    case 8: return rowp_launch_f<T, 3>(flags, a, st, sms);
-    case 16: return rowp_launch_f<T, 4>(flags, a, st, sms);
-    case 32: return rowp_launch_f<T, 5>(flags, a, st, sms);
-    case 64: return rowp_launch_f<T, 6>(flags, a, st, sms);
-    case 128: return rowp_launch_f<T, 7>(flags, a, st, sms);
-    case 256: return rowp_launch_f<T, 8>(flags, a, st, sms);
-    case 512: return rowp_launch_f<T, 9>(flags, a, st, sms);
-    case 1024: return rowp_launch_f<T, 10>(flags, a, st, sms);
-    case 2048: return rowp_launch_f<T, 11>(flags, a, st, sms);
-    case 4096: return rowp_launch_f<T, 12>(flags, a, st, sms);
+    case 8: return rowp_launch_n<T, 3, F>(a, st, sms);
+    case 16: return rowp_launch_n<T, 4, F>(a, st, sms);
+    case 32: return rowp_launch_n<T, 5, F>(a, st, sms);
+    case 64: return rowp_launch_n<T, 6, F>(a, st, sms);
+    case 128: return rowp_launch_n<T, 7, F>(a, st, sms);
+    case 256: return rowp_launch_n<T, 8, F>(a, st, sms);
+    case 512: return rowp_launch_n<T, 9, F>(a, st, sms);
+    case 1024: return rowp_launch_n<T, 10, F>(a, st, sms);
+    case 2048: return rowp_launch_n<T, 11, F>(a, st, sms);
+    case 4096: return rowp_launch_n<T, 12, F>(a, st, sms);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -141,10 +117,12 @@ template <class T> cudaError_t launch_ref_R(bool imag, const RowArgs &a, cudaStr
   return cudaGetLastError();
 }
 
-#define SPGPE_INSTANTIATE_ROW(T)                                                    \
+#define SPGPE_INSTANTIATE_ROW_SHAPE(T)                                              \
   template LaunchShape row_shape<T>(int, int);                                      \
-  template cudaError_t launch_row<T>(int, RowArgs, cudaStream_t);                   \
-  template cudaError_t launch_ref_R<T>(bool, const RowArgs &, cudaStream_t);         \
-  template cudaError_t launch_row_p<T>(int, RowArgs, cudaStream_t, int);
+  template cudaError_t launch_ref_R<T>(bool, const RowArgs &, cudaStream_t);
+
+#define SPGPE_INSTANTIATE_ROW_FLAG(T, F)                                            \
+  template cudaError_t launch_row_f<T, F>(RowArgs, cudaStream_t);                   \
+  template cudaError_t launch_row_pf<T, F>(RowArgs, cudaStream_t, int);
 
 }  // namespace spgpe

@@ -343,8 +343,9 @@ def test_error_statuses():
             c.step_real(t, float("nan"), 1)
         with pytest.raises(sp.SpgpeError, match="EINVAL"):
             c.set_potentials(np.full((32, 32), np.inf))
-        with pytest.raises(sp.SpgpeError, match="EINVAL"):
-            c.step_imag(t, 1e-3, 1, norm_mode=5)
+        for bad in (2, 3, 6, 7):  # a normalisation mode other than TOTAL / PER_COMPONENT (| LAGGED)
+            with pytest.raises(sp.SpgpeError, match="EINVAL"):
+                c.step_imag(t, 1e-3, 1, norm_mode=bad)
         z = torch.zeros_like(t)
         with pytest.raises(sp.SpgpeError, match="ENONFINITE"):
             c.step_imag(z, 1e-3, 3, sp.SPGPE_NORM_TOTAL, residual=True)
