@@ -60,6 +60,8 @@ struct spgpe_ctx {
   unsigned *d_counters = nullptr;
   double *d_scale = nullptr;
   double *d_scale2 = nullptr;  // second scale buffer of the lagged renormalisation
+  void *d_scale_t = nullptr;   // both scale buffers in the working precision, [2][ninst][2]
+  void *d_cfac = nullptr;      // [ninst][2] working precision: the lagged column pass's correction
   int *d_flags = nullptr;
   int *d_active = nullptr;    // [ninst] per-instance step mask (relaxation freezes converged instances)
   bool use_active = false;
@@ -180,8 +182,8 @@ void free_all(spgpe_ctx *c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   void *ps[] = {c->d_twx, c->d_twy, c->d_twe, c->d_tabx, c->d_taby, c->d_rawx, c->d_rawy, c->d_pot2d, c->d_kxt,
-                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_scale2, c->d_flags, c->d_active,
-                c->d_scratch, c->d_stage};
+                c->d_kyt, c->d_gpar, c->d_partials, c->d_counters, c->d_scale, c->d_scale2, c->d_scale_t,
+                c->d_cfac, c->d_flags, c->d_active, c->d_scratch, c->d_stage};
   for (void *p : ps)
     if (p) cudaFree(p);
   if (c->plan_ok) cufftDestroy(c->plan);
@@ -261,7 +263,8 @@ int upload_raw(spgpe_ctx *c) {
 
 // Step tables for substep dt (real or imaginary time):
 //   x/y step tables {V + delta/2, V - delta/2, X constants} of the separable
-//   pieces, X constants for the angle a = Omega_piece dt / 8 of X(dt/4):
+//   pieces (imaginary time: exp(-(dt/2) (V +- delta/2)), the potential
+//   factors of D(dt/2), which multiply to the factor of the sum), X constants for the angle a = Omega_piece dt / 8 of X(dt/4):
 //   (tan(a/2), sin a) in real time (three-shear rotation), (cosh a - 1,
 //   sinh a) in imaginary time (to full relative precision);
 //   K tables a_j(kx) - 1 with a_j = exp(-i dt (kx^2/2 -+ kL kx)) and b(ky) - 1
@@ -294,19 +297,22 @@ int ensure_tables(spgpe_ctx *c, double dt, int imag) {
       o[1] = -std::sin(th);
     }
   };
+  // potential entries: V +- delta/2 (real time), or the factors
+  // exp(-(dt/2) (V +- delta/2)) of D(dt/2) in imaginary time
+  auto pot = [&](double v) { return imag ? std::exp(-0.5 * dt * v) : v; };
   for (int i = 0; i < ni; ++i) {
     for (int x = 0; x < nx; ++x) {
       const double *h = &c->hx[((size_t)i * nx + x) * 3];
       double *o = &tx[((size_t)i * nx + x) * 4];
-      o[0] = h[0] + 0.5 * h[1];
-      o[1] = h[0] - 0.5 * h[1];
+      o[0] = pot(h[0] + 0.5 * h[1]);
+      o[1] = pot(h[0] - 0.5 * h[1]);
       rot(h[2] * dt / 8.0, o[2], o[3]);
     }
     for (int y = 0; y < ny; ++y) {
       const double *h = &c->hy[((size_t)i * ny + y) * 3];
       double *o = &ty[((size_t)i * ny + y) * 4];
-      o[0] = h[0] + 0.5 * h[1];
-      o[1] = h[0] - 0.5 * h[1];
+      o[0] = pot(h[0] + 0.5 * h[1]);
+      o[1] = pot(h[0] - 0.5 * h[1]);
       rot(h[2] * dt / 8.0, o[2], o[3]);
     }
   }
@@ -367,6 +373,10 @@ RowArgs row_args(spgpe_ctx *c, void *psi, double dt) {
   a.partials = c->d_partials;
   a.counters = c->d_counters;
   a.scale = c->d_scale;
+  a.scale_t = c->d_scale_t;
+  a.scale_pred = c->d_scale2;
+  a.scale_pred_t = static_cast<char *>(c->d_scale_t) + (size_t)c->ninst * 2 * (c->es / 2);
+  a.cfac = nullptr;
   a.tgt0 = 0.5;
   a.tgt1 = 0.5;
   a.norm_mode = 0;
@@ -399,6 +409,9 @@ void restrict_row(const spgpe_ctx *c, RowArgs &a, int i0, int ni) {
   a.counters = skip(a.counters, i * sizeof(unsigned));
   a.scale = skip(a.scale, i * 2 * sizeof(double));
   a.scale_pred = skip(a.scale_pred, i * 2 * sizeof(double));
+  a.scale_t = skip(a.scale_t, i * 2 * (es / 2));
+  a.scale_pred_t = skip(a.scale_pred_t, i * 2 * (es / 2));
+  a.cfac = skip(a.cfac, i * 2 * (es / 2));
   a.active = skip(a.active, i * sizeof(int));
   a.ninst = ni;
 }
@@ -407,8 +420,7 @@ void restrict_col(const spgpe_ctx *c, ColArgs &a, int i0, int ni) {
   const size_t es = c->es, i = (size_t)i0;
   a.psi = skip(a.psi, i * 2 * c->plane() * es);
   a.kxt = skip(a.kxt, i * 2 * c->nx * es);
-  a.cnum = skip(a.cnum, i * 2 * sizeof(double));
-  a.cden = skip(a.cden, i * 2 * sizeof(double));
+  a.cfac = skip(a.cfac, i * 2 * (es / 2));
   a.active = skip(a.active, i * sizeof(int));
   a.ninst = ni;
 }
@@ -672,6 +684,8 @@ int init_common(spgpe_ctx **out, int nx, int ny, double xmax, double ymax, int n
       (r = dev_alloc(c, (void **)&c->d_counters, (size_t)ninst * sizeof(unsigned))) ||
       (r = dev_alloc(c, (void **)&c->d_scale, (size_t)ninst * 2 * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_scale2, (size_t)ninst * 2 * sizeof(double))) ||
+      (r = dev_alloc(c, &c->d_scale_t, (size_t)2 * ninst * 2 * sizeof(double))) ||
+      (r = dev_alloc(c, &c->d_cfac, (size_t)ninst * 2 * sizeof(double))) ||
       (r = dev_alloc(c, (void **)&c->d_flags, sizeof(int))) ||
       (r = dev_alloc(c, (void **)&c->d_active, (size_t)ninst * sizeof(int)))) {
     g_init_error = c->err;
@@ -758,15 +772,17 @@ int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, 
   ra.tgt0 = t0;
   ra.tgt1 = t1;
   ra.norm_mode = norm_mode;
-  ra.scale_pred = c->d_scale2;
+  ra.cfac = c->d_cfac;
   ColArgs ca = col_args(c, p);
-  double *sc[2] = {c->d_scale, c->d_scale2};
   if (ni >= 0) {  // a chunk of instances (host pipeline; no residual)
     restrict_row(c, ra, i0, ni);
     restrict_col(c, ca, i0, ni);
-    sc[0] = ra.scale;
-    sc[1] = const_cast<double *>(ra.scale_pred);
   }
+  // the two scale buffers (FP64 and working precision) and the correction
+  double *sc[2] = {ra.scale, const_cast<double *>(ra.scale_pred)};
+  void *st[2] = {ra.scale_t, const_cast<void *>(ra.scale_pred_t)};
+  void *cf = ra.cfac;
+  ra.cfac = nullptr;
   // sc[last]: the buffer holding the most recent exact scale
   int last = 0;
   if (nsteps == 1 && residual) {
@@ -779,6 +795,7 @@ int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, 
     const bool into_residual_step = residual && s == nsteps - 1;
     if (!lagged || s == 1 || into_residual_step) {
       ra.scale = sc[0];
+      ra.scale_t = st[0];
       CK(c, row(c, kImagA, ra));
       last = 0;
       if (into_residual_step) {
@@ -793,16 +810,19 @@ int imag_enqueue(spgpe_ctx *c, void *p, double dtau, int nsteps, int norm_mode, 
     } else {
       RowArgs rl = ra;
       rl.scale_pred = sc[last];
+      rl.scale_pred_t = st[last];
       rl.scale = sc[last ^ 1];
+      rl.scale_t = st[last ^ 1];
+      rl.cfac = cf;
       CK(c, row(c, kImagLag, rl));
       ColArgs cl = ca;
-      cl.cnum = sc[last ^ 1];
-      cl.cden = sc[last];
+      cl.cfac = cf;
       CK(c, col(c, true, cl));
       last ^= 1;
     }
   }
   ra.scale = sc[0];
+  ra.scale_t = st[0];
   CK(c, row(c, kImagA, ra));
   CK(c, row(c, kImagScale, ra));
   if (residual) {
@@ -1626,9 +1646,12 @@ extern "C" int spgpe_relax(spgpe_ctx *c, void *psi, double dtau, double tol, int
       ++launches;
     }
   }
-  // the context's own precision (a staged host spinor is already on the device)
-  r = relax_stage(c, mem, c->ninst, dtau, tol, max_steps, check_every, norm_mode, t0, t1, false, give_up, lagged,
-                  res, &s, &launches);
+  // the context's own precision (a staged host spinor is already on the device),
+  // with what is left of the step budget
+  const int left = std::max(0, max_steps - s64);
+  if (left > 0)
+    r = relax_stage(c, mem, c->ninst, dtau, tol, left, check_every, norm_mode, t0, t1, false, give_up, lagged,
+                    res, &s, &launches);
   if (r) return r;
   if (!c->cls.empty() && (r = join_classes(c))) return r;
   c->last_launches = launches;

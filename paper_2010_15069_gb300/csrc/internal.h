@@ -37,6 +37,8 @@ struct RowArgs {
   void *psi;              // [ninst][2][ny][nx] complex, in place
   const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, X constants} step table
   const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, X constants} step table
+                          // (imaginary time: the factors exp(-tau (V +- delta/2)) of the
+                          // separable pieces in place of the potentials)
                           // X constants: (tan(a/2), sin a) in real time, (cosh a - 1, sinh a)
                           // in imaginary time, a = Omega piece * dt / 8
   const void *pot2d;      // [ny][nx] {V+delta/2, V-delta/2, Omega, 0} or null
@@ -51,8 +53,12 @@ struct RowArgs {
   int omega_pieces;       // bit 0: some Omega_y != 0, bit 1: some Omega_x != 0 (separable pieces)
   double *partials;       // [ninst][gridDim.x][2]
   unsigned *counters;     // [ninst], zero between launches
-  double *scale;          // [ninst][2]: written by the last unit of F_PART, read by F_SCALE
-  const double *scale_pred;  // [ninst][2]: the predicted scale F_LAG applies (never the buffer written)
+  double *scale;          // [ninst][2]: written by the last unit of F_PART
+  void *scale_t;          // [ninst][2] the same in the working precision (read by F_SCALE)
+  const double *scale_pred;    // [ninst][2]: the predicted scale of F_LAG (never the buffer written)
+  const void *scale_pred_t;    // the same in the working precision (what F_LAG applies)
+  void *cfac;             // [ninst][2] working precision, F_LAG only: the last unit writes
+                          // scale / scale_pred, the column pass's correction (null otherwise)
   double tgt0, tgt1;      // target atom numbers
   int norm_mode;          // 0 total, 1 per component
   double wgt;             // dx * dy
@@ -72,9 +78,9 @@ struct ColArgs {
   const void *kyt;        // [ny] complex b(ky) - 1 (1/(nx ny) applied in the kernel)
   const void *tw;         // twiddle table of the y plan (see TwType in fft_core.cuh)
   // Lagged renormalisation: each column of instance i, component j is also
-  // multiplied by cnum[2 i + j] / cden[2 i + j] (the exact scale over the
-  // predicted one); null: no such factor.
-  const double *cnum, *cden;
+  // multiplied by cfac[2 i + j] (working precision: the exact scale over the
+  // predicted one, written by the row pass before); null: no such factor.
+  const void *cfac;
   int nx, ny, ninst, C;
 };
 

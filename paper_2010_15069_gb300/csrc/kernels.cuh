@@ -80,30 +80,44 @@ template <class T> __device__ __forceinline__ cx<T> add_mul1(cx<T> z, cx<T> w) {
   return {z.re + d_fma(z.re, w.re, -(z.im * w.im)), z.im + d_fma(z.re, w.im, z.im * w.re)};
 }
 
+// expm1 of the single-precision general tier, out of line (imaginary-time
+// warps whose interaction exponent exceeds the series bound: rare, so one
+// shared copy keeps the passes within the instruction cache).
+static __device__ __noinline__ float expm1_general(float x) { return expm1_f(x); }
+__device__ __forceinline__ double expm1_general(double x) { return expm1(x); }
+
 // D(tau): diagonal potential + mean-field phase (decay), densities on entry.
 // htau = -tau/2 in real time (the half phase), -tau in imaginary time.
+// Real time: vu, vd are V +- delta/2 and the phase is the whole exponent.
+// Imaginary time: vu, vd are the potential factors exp(-tau (V +- delta/2))
+// (from the step tables) and only the interaction exponent -tau (g11 rho_up +
+// g12 rho_dn) (resp. down) goes through expm1: exp(-tau (V + g rho)) =
+// exp(-tau V) (1 + expm1(-tau g rho)).
 // TIER (the caller has checked it for every point of the warp): 0: |htau e|
-// < 1/64, 1: |htau e| < 1/8 (imaginary time: < 1/2), so the series need no
-// range reduction; 2: any phase.  FP64 always takes the library functions.
+// < 1/64, 1: |htau e| < 1/8 (imaginary time: < 1/2, e the interaction part),
+// so the series need no range reduction; 2: any phase.  FP64 always takes the
+// library functions.
 template <bool IMAG, int TIER = 2, class T>
 __device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T htau) {
   constexpr bool F32 = sizeof(T) == 4;
   const T ru = d_fma(u.re, u.re, u.im * u.im), rd = d_fma(d.re, d.re, d.im * d.im);
-  const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
-  const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
-  const T hu = htau * eu, hd = htau * ed;
   if constexpr (IMAG) {
+    const T hu = htau * d_fma(g12, rd, g11 * ru), hd = htau * d_fma(g12, ru, g22 * rd);
     T fu, fd;
     if constexpr (F32 && TIER < 2) {
       fu = expm1_small(hu);
       fd = expm1_small(hd);
     } else {
-      fu = expm1_f(hu);
-      fd = expm1_f(hd);
+      fu = expm1_general(hu);
+      fd = expm1_general(hd);
     }
-    u = {d_fma(u.re, fu, u.re), d_fma(u.im, fu, u.im)};
-    d = {d_fma(d.re, fd, d.re), d_fma(d.im, fd, d.im)};
+    const T au = d_fma(vu, fu, vu), ad = d_fma(vd, fd, vd);  // exp(-tau V) (1 + expm1(-tau g rho))
+    u = {u.re * au, u.im * au};
+    d = {d.re * ad, d.im * ad};
   } else {
+    const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
+    const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
+    const T hu = htau * eu, hd = htau * ed;
     // the phases exp(-i tau e) as three-shear rotations by 2 h, h = htau e
     // (determinant one: no systematic change of |psi| from rounded constants)
     T tu, su, td, sd;
@@ -318,12 +332,23 @@ __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4
   constexpr bool IMAG = (F & F_IMAG) != 0;
   constexpr bool MERGE = !IMAG && (F & F_REND) && (F & F_RSTART) && !(F & F_PART);
   const q4<T> px = tab[x];
-  T vu = px.x + ty.x, vd = px.y + ty.y;
-  T q2z = T(0);
+  T vu, vd, q2z = T(0);
+  if constexpr (IMAG) {  // potential factors exp(-tau (V +- delta/2)) of the separable pieces
+    vu = px.x * ty.x;
+    vd = px.y * ty.y;
+  } else {
+    vu = px.x + ty.x;
+    vd = px.y + ty.y;
+  }
   if (p2) {
     const q4<T> q = p2[(long)y * N + x];
-    vu += q.x;
-    vd += q.y;
+    if constexpr (IMAG) {
+      vu *= exp(htau * q.x);
+      vd *= exp(htau * q.y);
+    } else {
+      vu += q.x;
+      vd += q.y;
+    }
     q2z = q.z;
   }
   const XPoint<T> xc = xpoint<IMAG, T>(px, ty, p2 != nullptr, q2z, xang);
@@ -385,7 +410,7 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
   constexpr bool IMAG = (F & F_IMAG) != 0;
   if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 1>(v, t, a.tw, acc);
   if constexpr (F & F_SCALE) {
-    const T sc = T(a.scale[2 * inst + comp]);
+    const T sc = reinterpret_cast<const T *>(a.scale_t)[2 * inst + comp];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[0][m] = cscale(v[0][m], sc);
   }
@@ -401,8 +426,8 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     T tm = T(0), sm = T(0);
     T su = T(1), sd = T(1);
     if constexpr ((F & F_LAG) != 0) {
-      su = T(a.scale_pred[2 * inst]);
-      sd = T(a.scale_pred[2 * inst + 1]);
+      su = reinterpret_cast<const T *>(a.scale_pred_t)[2 * inst];
+      sd = reinterpret_cast<const T *>(a.scale_pred_t)[2 * inst + 1];
     }
     bool ymerge = false;
     if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
@@ -427,7 +452,9 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     // (the lagged pass scales the densities between R_end and R_start by the
     // squared predicted scale)
     if constexpr ((F & F_LAG) != 0) rmax *= fmax(T(1), fmax(su * su, sd * sd));
-    const T hb = fabs(htau) * (gp[3] + gmax * T(1.05) * rmax);
+    // (imaginary time: the potential factors come from tables, so only the
+    // interaction exponent is bounded; real time: the whole phase)
+    const T hb = fabs(htau) * ((IMAG ? T(0) : gp[3]) + gmax * T(1.05) * rmax);
     const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
     const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
 #define SPGPE_R_POINTS(TIER) \
@@ -501,6 +528,24 @@ __device__ __forceinline__ unsigned count_group(unsigned *counter) {
   return old;
 }
 
+// The last row group of an instance publishes its renormalisation scale: in
+// FP64, in the working precision (what F_SCALE and F_LAG multiply by), and
+// for a lagged pass the column pass's correction scale / predicted scale; it
+// then rearms the instance's counter.
+template <class T> __device__ __forceinline__ void write_scale(const RowArgs &a, int inst, double s0, double s1) {
+  a.scale[2 * inst] = s0;
+  a.scale[2 * inst + 1] = s1;
+  T *st = reinterpret_cast<T *>(a.scale_t);
+  st[2 * inst] = T(s0);
+  st[2 * inst + 1] = T(s1);
+  if (a.cfac) {
+    T *cf = reinterpret_cast<T *>(a.cfac);
+    cf[2 * inst] = T(s0 / a.scale_pred[2 * inst]);
+    cf[2 * inst + 1] = T(s1 / a.scale_pred[2 * inst + 1]);
+  }
+  a.counters[inst] = 0u;
+}
+
 // Atom-number partials of one row group; the last group of the instance to
 // finish reduces them in a fixed order (FP64) and writes the
 // renormalisation scale (Sec. 3.2).  Called by every thread of the block.
@@ -534,9 +579,7 @@ __device__ __forceinline__ void row_partials(const RowArgs &a, int inst, int gro
         s0 = s1 = sqrt((a.tgt0 + a.tgt1) / (nu + nd));
       }
       if (!isfinite(s0) || !isfinite(s1)) atomicOr(a.flags, 1);
-      a.scale[2 * inst] = s0;
-      a.scale[2 * inst + 1] = s1;
-      a.counters[inst] = 0u;
+      write_scale<T>(a, inst, s0, s1);
     }
   }
   __syncthreads();
@@ -599,11 +642,9 @@ row_pass(const RowArgs a) {
 // inverse transform's 1/(nx ny), times the correction s_n / s_{n-1} of the
 // lagged renormalisation when there is one.
 template <class T> __device__ __forceinline__ T col_inv(const ColArgs &a, int pc) {
-  if constexpr (sizeof(T) == 4) {
-    return a.cnum ? (float)(a.inv_d * (a.cnum[pc] / a.cden[pc])) : a.inv_f;
-  } else {
-    return a.cnum ? a.inv_d * (a.cnum[pc] / a.cden[pc]) : a.inv_d;
-  }
+  T inv;
+  if constexpr (sizeof(T) == 4) inv = a.inv_f; else inv = a.inv_d;
+  return a.cfac ? inv * reinterpret_cast<const T *>(a.cfac)[pc] : inv;
 }
 
 // Column-pass compute on registers already loaded: forward y-FFT, K(dt) with
@@ -805,16 +846,28 @@ __global__ void __launch_bounds__(256) ref_R_kernel(const RowArgs a) {
   cx<T> *d = u + plane;
   const q4<T> px = reinterpret_cast<const q4<T> *>(a.tabx)[(long)inst * a.nx + x];
   const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
-  T vu = px.x + ty.x, vd = px.y + ty.y, q2z = T(0);
+  T htau, xang;
+  if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
+  T vu, vd, q2z = T(0);
+  if constexpr (IMAG) {
+    vu = px.x * ty.x;
+    vd = px.y * ty.y;
+  } else {
+    vu = px.x + ty.x;
+    vd = px.y + ty.y;
+  }
   const bool has2d = a.pot2d != nullptr;
   if (has2d) {
     const q4<T> q = reinterpret_cast<const q4<T> *>(a.pot2d)[i];
-    vu += q.x;
-    vd += q.y;
+    if constexpr (IMAG) {
+      vu *= exp(htau * q.x);
+      vd *= exp(htau * q.y);
+    } else {
+      vu += q.x;
+      vd += q.y;
+    }
     q2z = q.z;
   }
-  T htau, xang;
-  if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
   const XPoint<T> xc = xpoint<IMAG, T>(px, ty, has2d, q2z, xang);
   const int pieces = (a.omega_pieces & 3) | (has2d ? 4 : 0);
   const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;

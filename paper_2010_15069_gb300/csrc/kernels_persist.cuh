@@ -73,6 +73,7 @@ __device__ __forceinline__ unsigned warp_partials_post(const RowArgs &a, int ins
   return prev;
 }
 
+template <class T>
 __device__ __forceinline__ void warp_partials_finish(const RowArgs &a, int inst, int ngroups, unsigned prev) {
   const int lane = threadIdx.x & 31;
   prev = __shfl_sync(0xffffffffu, prev, 0);
@@ -98,9 +99,7 @@ __device__ __forceinline__ void warp_partials_finish(const RowArgs &a, int inst,
       s0 = s1 = sqrt((a.tgt0 + a.tgt1) / (nu + nd));
     }
     if (!isfinite(s0) || !isfinite(s1)) atomicOr(a.flags, 1);
-    a.scale[2 * inst] = s0;
-    a.scale[2 * inst + 1] = s1;
-    a.counters[inst] = 0u;
+    write_scale<T>(a, inst, s0, s1);
   }
 }
 
@@ -240,7 +239,7 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
     cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N + t;
 #pragma unroll
     for (int m = 0; m < E; ++m) p[m * TT] = v[0][m];
-    if constexpr ((F & F_PART) && U::WARP) warp_partials_finish(a, inst, upi, prev);
+    if constexpr ((F & F_PART) && U::WARP) warp_partials_finish<T>(a, inst, upi, prev);
     u = un;
   }
 }
