@@ -4,8 +4,10 @@
 // fno_kernels.cu.  Layout of activations: [batch][channel][n][n], x fastest.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -47,6 +49,9 @@ struct spgpe_fno {
   float *part = nullptr;
   size_t part_n = 0;
   double *sums = nullptr;
+  int *d_flags = nullptr;  // device error flags (a tensor-core wait that ran out)
+  double *bscr = nullptr;  // bias-gradient partial sums (64 per channel)
+  bool tensor_cores = true;  // SPGPE_FNO_TC=0 keeps every product on the CUDA cores
   std::vector<void *> allocs;
   std::string err;
 };
@@ -150,7 +155,7 @@ int ensure_workspace(spgpe_fno *f, int B, int n) {
       (r = falloc(f, &f->dh, hid)) || (r = falloc(f, &f->dv, act)) || (r = falloc(f, &f->dv2, act)) ||
       (r = falloc(f, &f->dout, (size_t)B * f->cout * P)) || (r = falloc(f, &f->oh, spec)) ||
       (r = falloc(f, &f->G, rows)) || (r = falloc(f, &f->doh, spec)) || (r = falloc(f, &f->part, f->part_n)) ||
-      (r = falloc(f, &f->sums, (size_t)2 * B)))
+      (r = falloc(f, &f->sums, (size_t)130 * B)))
     return r;
   f->ws_b = B;
   f->ws_n = n;
@@ -206,6 +211,23 @@ GemmC cg(int M, int N, int K, int batch, const void *A, bool bf, bool ca, long s
 
 const void *bfp(const spgpe_fno *f, long off) { return static_cast<const uint16_t *>(f->wb) + off; }
 
+// A real product of the model: the tensor-core path where it applies.
+cudaError_t greal(const spgpe_fno *f, GemmR g, cudaStream_t st) {
+  g.flags = f->tensor_cores ? f->d_flags : nullptr;
+  return gemm_real(g, st);
+}
+
+// Report (and clear) an error recorded on the device; after a synchronisation.
+int read_flags(spgpe_fno *f) {
+  int h = 0;
+  FCK(f, cudaMemcpy(&h, f->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    FCK(f, cudaMemset(f->d_flags, 0, sizeof(int)));
+    return ffail(f, SPGPE_ETIMEOUT, "a tensor-core wait ran out");
+  }
+  return SPGPE_OK;
+}
+
 // grad[M][N] += sum_b sum_p A[b](m, p) Bm[b](p, n): split-K over the points,
 // partials reduced in a fixed order.
 int wgrad(spgpe_fno *f, int M, int N, long P, int B, const float *A, long sAb, const float *Bm, long sBn, long sBb,
@@ -218,7 +240,7 @@ int wgrad(spgpe_fno *f, int M, int N, long P, int B, const float *A, long sAb, c
   g.splits = splits;
   g.partial = true;
   g.sCs = (long)M * N;
-  FCK(f, gemm_real(g, f->st));
+  FCK(f, greal(f, g, f->st));
   FCK(f, sum_splits(f->part, (long)M * N, B * splits, grad, true, f->st));
   return SPGPE_OK;
 }
@@ -235,11 +257,11 @@ int forward(spgpe_fno *f, const float *a, int B, int n, float *out) {
   g.sBb = (long)f->cin * P;
   g.sCb = WP;
   g.bias = f->wr + f->op;
-  FCK(f, gemm_real(g, st));
+  FCK(f, greal(f, g, st));
   for (int l = 0; l < f->L; ++l) {
     float *v = f->vs[l], *u = f->us[l];
     // along x: X1 = v Exr, computed as X1^T = Exr^T v^T (the long side as N)
-    FCK(f, gemm_real(rg(2 * M, B * W * n, n, f->Exr, false, 1, 2 * M, v, 1, n, f->X1, 1, 2 * M), st));
+    FCK(f, greal(f, rg(2 * M, B * W * n, n, f->Exr, false, 1, 2 * M, v, 1, n, f->X1, 1, 2 * M), st));
     const float2 *X1c = reinterpret_cast<const float2 *>(f->X1);
     // along y: vh = Ey X1 per (sample, channel)
     FCK(f, gemm_complex(cg(2 * M, M, n, B * W, f->Ey, false, false, n, 1, 0, X1c, false, M, 1, n * M, f->vh[l], M, 1,
@@ -253,7 +275,7 @@ int forward(spgpe_fno *f, const float *a, int B, int n, float *out) {
     FCK(f, gemm_complex(cg(n, M, 2 * M, B * W, f->Ey, false, true, 1, n, 0, f->oh, false, M, 1, SP, f->G, M, 1, n * M),
                         st));
     // real part of the inverse along x: u = G Exi
-    FCK(f, gemm_real(rg(B * W * n, n, 2 * M, reinterpret_cast<const float *>(f->G), false, 2 * M, 1, f->Exi, n, 1,
+    FCK(f, greal(f, rg(B * W * n, n, 2 * M, reinterpret_cast<const float *>(f->G), false, 2 * M, 1, f->Exi, n, 1,
                         u, n, 1),
                      st));
     // u += W_l v + w_l
@@ -263,7 +285,7 @@ int forward(spgpe_fno *f, const float *a, int B, int n, float *out) {
     g.sCb = WP;
     g.beta = 1.f;
     g.bias = f->wr + f->ow[l];
-    FCK(f, gemm_real(g, st));
+    FCK(f, greal(f, g, st));
     if (l < f->L - 1) {
       FCK(f, gelu_forward(u, f->vs[l + 1], (long)B * WP, st));
     } else {
@@ -276,14 +298,14 @@ int forward(spgpe_fno *f, const float *a, int B, int n, float *out) {
   g.sBb = WP;
   g.sCb = H * P;
   g.bias = f->wr + f->oq1;
-  FCK(f, gemm_real(g, st));
+  FCK(f, greal(f, g, st));
   FCK(f, gelu_forward(f->hp, f->h, (long)B * H * P, st));
   g = rg(f->cout, P, H, bfp(f, f->oQ2), true, H, 1, f->h, P, 1, out, P, 1);
   g.batch = B;
   g.sBb = H * P;
   g.sCb = (long)f->cout * P;
   g.bias = f->wr + f->oq2;
-  FCK(f, gemm_real(g, st));
+  FCK(f, greal(f, g, st));
   return SPGPE_OK;
 }
 
@@ -298,33 +320,33 @@ int gradient(spgpe_fno *f, const float *a, const float *target, int B, int n, fl
   FCK(f, loss_terms(out, target, C * P, B, f->sums, f->dout, st));
   // output layer
   if ((r = wgrad(f, C, H, P, B, f->dout, C * P, f->h, P, H * P, f->g + f->oQ2))) return r;
-  FCK(f, bias_gradient(f->dout, B, C, P, f->g + f->oq2, st));
+  FCK(f, bias_gradient(f->dout, B, C, P, f->g + f->oq2, f->bscr, st));
   GemmR g = rg(H, P, C, bfp(f, f->oQ2), true, 1, H, f->dout, P, 1, f->dh, P, 1);
   g.batch = B;
   g.sBb = C * P;
   g.sCb = H * P;
-  FCK(f, gemm_real(g, st));
+  FCK(f, greal(f, g, st));
   FCK(f, gelu_backward(f->hp, f->dh, (long)B * H * P, st));
   if ((r = wgrad(f, H, W, P, B, f->dh, H * P, f->vs[f->L], P, WP, f->g + f->oQ1))) return r;
-  FCK(f, bias_gradient(f->dh, B, H, P, f->g + f->oq1, st));
+  FCK(f, bias_gradient(f->dh, B, H, P, f->g + f->oq1, f->bscr, st));
   g = rg(W, P, H, bfp(f, f->oQ1), true, 1, W, f->dh, P, 1, f->dv, P, 1);
   g.batch = B;
   g.sBb = H * P;
   g.sCb = WP;
-  FCK(f, gemm_real(g, st));
+  FCK(f, greal(f, g, st));
   float *du = f->dv, *dvn = f->dv2;
   for (int l = f->L - 1; l >= 0; --l) {
     if (l < f->L - 1) FCK(f, gelu_backward(f->us[l], du, (long)B * WP, st));
     if ((r = wgrad(f, W, W, P, B, du, WP, f->vs[l], P, WP, f->g + f->oW[l]))) return r;
-    FCK(f, bias_gradient(du, B, W, P, f->g + f->ow[l], st));
+    FCK(f, bias_gradient(du, B, W, P, f->g + f->ow[l], f->bscr, st));
     // dv = W_l^T du
     g = rg(W, P, W, bfp(f, f->oW[l]), true, 1, W, du, P, 1, dvn, P, 1);
     g.batch = B;
     g.sBb = WP;
     g.sCb = WP;
-    FCK(f, gemm_real(g, st));
+    FCK(f, greal(f, g, st));
     // spectral part: dG = du Exi^T (into X1; as dG^T = Exi du^T), doh = Ey dG
-    FCK(f, gemm_real(rg(2 * M, B * W * n, n, f->Exi, false, n, 1, du, 1, n, f->X1, 1, 2 * M), st));
+    FCK(f, greal(f, rg(2 * M, B * W * n, n, f->Exi, false, n, 1, du, 1, n, f->X1, 1, 2 * M), st));
     const float2 *dG = reinterpret_cast<const float2 *>(f->X1);
     FCK(f, gemm_complex(cg(2 * M, M, n, B * W, f->Ey, false, false, n, 1, 0, dG, false, M, 1, n * M, f->doh, M, 1, SP),
                         st));
@@ -341,15 +363,16 @@ int gradient(spgpe_fno *f, const float *a, const float *target, int B, int n, fl
                         st));
     g = rg(B * W * n, n, 2 * M, reinterpret_cast<const float *>(f->G), false, 2 * M, 1, f->Exr, 1, 2 * M, dvn, n, 1);
     g.beta = 1.f;
-    FCK(f, gemm_real(g, st));
+    FCK(f, greal(f, g, st));
     std::swap(du, dvn);
   }
   if ((r = wgrad(f, W, f->cin, P, B, du, WP, a, P, (long)f->cin * P, f->g + f->oP))) return r;
-  FCK(f, bias_gradient(du, B, W, P, f->g + f->op, st));
+  FCK(f, bias_gradient(du, B, W, P, f->g + f->op, f->bscr, st));
   if (loss) {
     std::vector<double> s((size_t)2 * B);
     FCK(f, cudaMemcpyAsync(s.data(), f->sums, s.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     FCK(f, cudaStreamSynchronize(st));
+    if ((r = read_flags(f))) return r;
     double l = 0.0;
     for (int b = 0; b < B; ++b) l += s[2 * (size_t)b] / s[2 * (size_t)b + 1];
     *loss = l / B;
@@ -434,10 +457,18 @@ int spgpe_fno_create(spgpe_fno **out, int cin, int cout, int width, int modes, i
   int r;
   const size_t np = (size_t)o;
   if ((r = falloc(f, &f->w, np)) || (r = falloc(f, &f->wr, np)) || (r = falloc(f, &f->g, np)) ||
-      (r = falloc(f, &f->m, np)) || (r = falloc(f, &f->v, np)) || (r = falloc(f, (uint16_t **)&f->wb, np))) {
+      (r = falloc(f, &f->m, np)) || (r = falloc(f, &f->v, np)) || (r = falloc(f, (uint16_t **)&f->wb, np)) ||
+      (r = falloc(f, &f->d_flags, 1)) ||
+      (r = falloc(f, &f->bscr, (size_t)64 * std::max(std::max(width, hidden), std::max(cin, cout))))) {
     spgpe_fno_destroy(f);
     return r;
   }
+  if (cudaMemset(f->d_flags, 0, sizeof(int)) != cudaSuccess) {
+    spgpe_fno_destroy(f);
+    return SPGPE_ECUDA;
+  }
+  const char *tc = std::getenv("SPGPE_FNO_TC");
+  f->tensor_cores = !(tc && tc[0] == '0');
   std::vector<float> h;
   init_params(f, seed, h);
   if (spgpe_fno_set_params(f, h.data()) != SPGPE_OK) {
@@ -487,6 +518,7 @@ int spgpe_fno_gradient(spgpe_fno *f, const float *a, const float *target, int ba
   if (grad_host) {
     FCK(f, cudaMemcpyAsync(grad_host, f->g, (size_t)f->nparam * sizeof(float), cudaMemcpyDeviceToHost, f->st));
     FCK(f, cudaStreamSynchronize(f->st));
+    if ((r = read_flags(f))) return r;
   }
   return SPGPE_OK;
 }

@@ -301,45 +301,87 @@ __global__ void gelu_bwd(const float *__restrict__ u, float *__restrict__ d, lon
 }
 
 // grad[c] (+)= sum over samples b and points p of x[b][c][p] (fixed order).
-__global__ void __launch_bounds__(256) bias_grad(const float *__restrict__ x, int B, int C, long P, float *grad) {
-  const int c = blockIdx.x;
-  double s = 0.0;
-  for (int b = 0; b < B; ++b)
-    for (long p = threadIdx.x; p < P; p += blockDim.x) s += x[((long)b * C + c) * P + p];
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+// Bias gradient grad[c] += sum_b sum_p x[b][c][p], in two stages: kBiasSlices
+// blocks per channel each sum a contiguous slice of the points (float32 per
+// thread over at most a few dozen values, then a fixed tree), and one block
+// adds the slices of every channel in a fixed order in FP64.
+constexpr int kBiasSlices = 64;
+
+__global__ void __launch_bounds__(256) bias_grad_slices(const float *__restrict__ x, int B, int C, long P,
+                                                        double *part) {
+  const int c = blockIdx.x / kBiasSlices, sl = blockIdx.x - c * kBiasSlices;
+  const long n = (long)B * P, per = (n + kBiasSlices - 1) / kBiasSlices;
+  const long i0 = sl * per, i1 = min(n, i0 + per);
+  float s = 0.f;
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const long b = i / P, p = i - b * P;
+    s += x[(b * C + c) * P + p];
   }
-  if (threadIdx.x == 0) grad[c] += (float)red[0];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
 }
 
-// Per sample: num = sum (out - t)^2, den = sum t^2 (FP64) into sums[b][2].
-__global__ void __launch_bounds__(256) loss_sums(const float *__restrict__ out, const float *__restrict__ t, long n,
-                                                 double *sums) {
-  const int b = blockIdx.x;
-  double num = 0.0, den = 0.0;
-  for (long i = threadIdx.x; i < n; i += blockDim.x) {
-    const double o = out[(long)b * n + i], tv = t[(long)b * n + i];
-    num += (o - tv) * (o - tv);
-    den += tv * tv;
+__global__ void bias_grad_sum(const double *__restrict__ part, int C, float *grad) {
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double t = 0.0;
+    for (int sl = 0; sl < kBiasSlices; ++sl) t += part[(long)c * kBiasSlices + sl];
+    grad[c] += (float)t;
   }
-  __shared__ double r0[256], r1[256];
-  r0[threadIdx.x] = num;
-  r1[threadIdx.x] = den;
+}
+
+// Per sample: num = sum (out - t)^2, den = sum t^2 into sums[b][2], in two
+// stages like the bias gradient: kBiasSlices blocks per sample sum a slice
+// (float32 per thread, a fixed tree, FP64 across warps) into part[b][slice][2],
+// then one thread per sample adds the slices in a fixed order in FP64.
+__global__ void __launch_bounds__(256) loss_slices(const float *__restrict__ out, const float *__restrict__ t, long n,
+                                                   double *part) {
+  const int b = blockIdx.x / kBiasSlices, sl = blockIdx.x - b * kBiasSlices;
+  const long per = (n + kBiasSlices - 1) / kBiasSlices, i0 = sl * per, i1 = min(n, i0 + per);
+  float num = 0.f, den = 0.f;
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const float o = out[(long)b * n + i], tv = t[(long)b * n + i], d = o - tv;
+    num = fmaf(d, d, num);
+    den = fmaf(tv, tv, den);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  __shared__ float r0[8], r1[8];
+  if ((threadIdx.x & 31) == 0) {
+    r0[threadIdx.x >> 5] = num;
+    r1[threadIdx.x >> 5] = den;
+  }
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      r0[threadIdx.x] += r0[threadIdx.x + o];
-      r1[threadIdx.x] += r1[threadIdx.x + o];
-    }
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    sums[2 * b] = r0[0];
-    sums[2 * b + 1] = r1[0];
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += r0[w];
+      c += r1[w];
+    }
+    part[2 * (long)blockIdx.x] = a;
+    part[2 * (long)blockIdx.x + 1] = c;
+  }
+}
+
+__global__ void loss_sum(const double *__restrict__ part, int B, double *sums) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    double a = 0.0, c = 0.0;
+    for (int sl = 0; sl < kBiasSlices; ++sl) {
+      a += part[2 * ((long)b * kBiasSlices + sl)];
+      c += part[2 * ((long)b * kBiasSlices + sl) + 1];
+    }
+    sums[2 * b] = a;
+    sums[2 * b + 1] = c;
   }
 }
 
@@ -383,6 +425,8 @@ int grid_for(long n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4
 }  // namespace
 
 cudaError_t gemm_real(const GemmR &g, cudaStream_t st) {
+  // the pointwise channel maps with bfloat16 weights: tensor cores
+  if (gemm_tc_applies(g)) return gemm_real_tc(g, st);
   // large products: the register-tiled kernel (BM = 128, or 64 when M is small)
   if (g.N >= 128 && g.M >= 64) {
     const int bm = g.M >= 128 ? 128 : 64;
@@ -447,13 +491,16 @@ cudaError_t gelu_backward(const float *u, float *d, long n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t bias_gradient(const float *x, int B, int C, long P, float *grad, cudaStream_t st) {
-  bias_grad<<<C, 256, 0, st>>>(x, B, C, P, grad);
+cudaError_t bias_gradient(const float *x, int B, int C, long P, float *grad, double *scratch, cudaStream_t st) {
+  bias_grad_slices<<<C * kBiasSlices, 256, 0, st>>>(x, B, C, P, scratch);
+  bias_grad_sum<<<1, 256, 0, st>>>(scratch, C, grad);
   return cudaGetLastError();
 }
 
 cudaError_t loss_terms(const float *out, const float *t, long n, int B, double *sums, float *dout, cudaStream_t st) {
-  loss_sums<<<B, 256, 0, st>>>(out, t, n, sums);
+  double *part = sums + 2 * (long)B;
+  loss_slices<<<B * kBiasSlices, 256, 0, st>>>(out, t, n, part);
+  loss_sum<<<1, 256, 0, st>>>(part, B, sums);
   if (dout) loss_grad<<<grid_for(n * B), 256, 0, st>>>(out, t, n, B, sums, dout);
   return cudaGetLastError();
 }

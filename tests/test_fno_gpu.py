@@ -85,3 +85,26 @@ def test_training_learns_a_teacher_network():
         t = teacher.forward(a)
         losses = [student.train_step(a, t, 3e-3) for _ in range(200)]
     assert losses[-1] < 0.05 * losses[0]
+
+
+def test_tensor_core_products_agree_with_the_cuda_core_products(monkeypatch):
+    """The pointwise channel maps with bfloat16 weights run on the tensor cores
+    (tcgen05: the float32 activations split into three bfloat16 terms, float32
+    accumulation in tensor memory); SPGPE_FNO_TC=0 keeps them on the CUDA cores.
+    At the warm start's architecture on a 128^2 grid (128 tiles of 128 points
+    per sample) both give the forward pass and every gradient to float32
+    accumulation error."""
+    sh, _, theta, a, t = setup(FULL, 128, 2, 13)
+    res = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("SPGPE_FNO_TC", mode)
+        with sp.FNO(**FULL, seed=13) as f:
+            f.set_params(theta.astype(np.float32))
+            ad, td = torch.from_numpy(a).cuda(), torch.from_numpy(t).cuda()
+            loss, g, out = f.gradient(ad, td)
+            res[mode] = (loss, g, out.cpu().numpy())
+    assert rel(res["1"][2], res["0"][2]) < 1e-5
+    assert abs(res["1"][0] - res["0"][0]) < 1e-5 * res["0"][0]
+    g1, g0 = sh.unpack(res["1"][1]), sh.unpack(res["0"][1])
+    for name, _ in sh.layout():
+        assert rel(g1[name], g0[name]) < 1e-4, name
