@@ -57,7 +57,8 @@ enum {
   SPGPE_ECUDA = -3,      /* a CUDA runtime call failed; see spgpe_last_error */
   SPGPE_ENONFINITE = -4, /* a norm or energy reduction met NaN/Inf (or a zero norm) */
   SPGPE_ETIMEOUT = -5,   /* a bounded device wait gave up (a tile transfer never landed) */
-  SPGPE_ESTATE = -6      /* call out of order (e.g. stepping before potentials) */
+  SPGPE_ESTATE = -6,     /* call out of order (e.g. stepping before potentials) */
+  SPGPE_EBOUNDS = -7     /* an index fell outside its buffer (bounds-checked builds only) */
 };
 
 typedef struct spgpe_ctx spgpe_ctx;

@@ -18,7 +18,7 @@ SPGPE_IMAG_LAGGED = 4
 SPGPE_RELAX_LADDER, SPGPE_RELAX_GIVE_UP, SPGPE_RELAX_LAGGED = 1, 2, 4
 SPGPE_OK, SPGPE_ETIMEOUT = 0, -5
 STATUS = {0: "SPGPE_OK", -1: "SPGPE_EINVAL", -2: "SPGPE_ENOMEM", -3: "SPGPE_ECUDA",
-          -4: "SPGPE_ENONFINITE", -5: "SPGPE_ETIMEOUT", -6: "SPGPE_ESTATE"}
+          -4: "SPGPE_ENONFINITE", -5: "SPGPE_ETIMEOUT", -6: "SPGPE_ESTATE", -7: "SPGPE_EBOUNDS"}
 
 # Every entry point declared in include/spgpe.h, with its ctypes signature.
 _P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -72,9 +72,13 @@ class SpgpeError(RuntimeError):
         self.code = code
 
 
-def load(path: str = LIB_PATH):
-    """Load libspgpe.so (raises if it is missing: there is no CPU fallback)."""
+def load(path: str | None = None):
+    """Load libspgpe.so (raises if it is missing: there is no CPU fallback).
+    SPGPE_LIBRARY names another build of the same library (the bounds-checked
+    one, libspgpe_bounds.so) for a process that wants it."""
     global _lib
+    if path is None:
+        path = os.environ.get("SPGPE_LIBRARY") or LIB_PATH
     with _lock:
         if _lib is None:
             if not os.path.exists(path):

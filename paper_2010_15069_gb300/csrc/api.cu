@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "spgpe.h"
+#include "async_copy.cuh"
 #include "internal.h"
 #include "twiddles.h"
 
@@ -639,7 +640,9 @@ int read_flags(spgpe_ctx *c) {
   CK(c, cudaStreamSynchronize(c->st));
   if (h) {
     CK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int), c->st));
-    if (h & 2) return fail(c, SPGPE_ETIMEOUT, "a tile transfer did not complete within the wait limit");
+    if (h & kErrBounds)
+      return fail(c, SPGPE_EBOUNDS, "an index fell outside its buffer (bounds-checked build; the access was skipped)");
+    if (h & kErrTimeout) return fail(c, SPGPE_ETIMEOUT, "a tile transfer did not complete within the wait limit");
     return fail(c, SPGPE_ENONFINITE, "non-finite or zero atom number met during imaginary-time renormalisation");
   }
   return SPGPE_OK;

@@ -14,6 +14,25 @@ namespace spgpe {
 
 constexpr long long kWaitCycles = 1ll << 31;
 constexpr int kErrTimeout = 2;  // bit in the context's error flags
+constexpr int kErrBounds = 4;   // bit in the context's error flags (bounds-checked builds only)
+
+// Index check of the bounds-checked build (compiled with -DSPGPE_BOUNDS, the
+// stand-in for a memory checker): an index i outside [0, n) sets kErrBounds in
+// the error flags and the caller skips the access.  In the release build it is
+// the constant true, so the kernels are unchanged.
+__device__ __forceinline__ bool in_bounds(int *flags, long i, long n) {
+#ifdef SPGPE_BOUNDS
+  if (i < 0 || i >= n) {
+    atomicOr(flags, kErrBounds);
+    return false;
+  }
+#else
+  (void)flags;
+  (void)i;
+  (void)n;
+#endif
+  return true;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

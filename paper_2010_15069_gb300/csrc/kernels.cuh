@@ -16,6 +16,7 @@
 
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "fastmath.cuh"
 #include "fft_core.cuh"
 #include "internal.h"
@@ -415,7 +416,10 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     for (int m = 0; m < E; ++m) v[0][m] = cscale(v[0][m], sc);
   }
   if constexpr (F & (F_REND | F_RSTART)) {
-    const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[(long)inst * a.ny + y];
+    // (bounds-checked build: a bad row index is recorded and replaced by 0, so
+    // that every thread still reaches the warp's barriers)
+    const long tyi = in_bounds(a.flags, (long)inst * a.ny + y, (long)a.ninst * a.ny) ? (long)inst * a.ny + y : 0;
+    const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[tyi];
     const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
     const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
     const T g11 = gp[0], g22 = gp[1], g12 = gp[2];
@@ -555,8 +559,11 @@ __device__ __forceinline__ void row_partials(const RowArgs &a, int inst, int gro
   double nsum[2];
   block_sum_pair<T>(tsum, nsum);
   if (threadIdx.x == 0) {
-    a.partials[((long)inst * ngroups + group) * 2] = nsum[0];
-    a.partials[((long)inst * ngroups + group) * 2 + 1] = nsum[1];
+    if (in_bounds(a.flags, ((long)inst * ngroups + group) * 2 + 1, (long)a.ninst * a.ny * 2) &&
+        in_bounds(a.flags, inst, a.ninst)) {
+      a.partials[((long)inst * ngroups + group) * 2] = nsum[0];
+      a.partials[((long)inst * ngroups + group) * 2 + 1] = nsum[1];
+    }
     const unsigned prev = count_group(&a.counters[inst]);
     s_last = (prev == (unsigned)ngroups - 1u);
   }
@@ -625,15 +632,17 @@ row_pass(const RowArgs a) {
   const RowAcc<T, row_warp_local(TT)> acc{sm + pl.lrow * row_stride(N, sizeof(cx<T>)) + pl.comp * PADN, 0,
                                           pl.mask};
 
+  const long pbase = (((long)inst * 2 + pl.comp) * a.ny + y) * N, ptotal = (long)a.ninst * 2 * a.ny * N;
   cx<T> v[1][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[0][m] = p[pl.t + m * TT];
+  for (int m = 0; m < E; ++m) v[0][m] = in_bounds(a.flags, pbase + pl.t + m * TT, ptotal) ? p[pl.t + m * TT] : cx<T>{};
   T nsum[2] = {T(0), T(0)};
   row_compute<T, LOGN, LOGE, F>(v, pl.t, pl.comp, pl.mask, pl.half, inst, y, acc,
                                 reinterpret_cast<const q4<T> *>(a.tabx) + (long)inst * N, a, nsum);
   if constexpr (F & F_PART) row_partials<T>(a, inst, blockIdx.x, gridDim.x, nsum);
 #pragma unroll
-  for (int m = 0; m < E; ++m) p[pl.t + m * TT] = v[0][m];
+  for (int m = 0; m < E; ++m)
+    if (in_bounds(a.flags, pbase + pl.t + m * TT, ptotal)) p[pl.t + m * TT] = v[0][m];
 }
 
 // ---------------------------------------------------------- column pass
@@ -691,14 +700,18 @@ __global__ void __launch_bounds__(512) col_pass(const ColArgs a) {
   const ColAcc<T> acc{reinterpret_cast<cx<T> *>(smem_raw), C, c};
   const int rs = TT * a.nx;  // element offset between a thread's rows (fits in 32 bits)
 
+  const long cbase = ((long)inst * 2 + comp) * (long)N * a.nx + kx, ctotal = (long)a.ninst * 2 * N * a.nx;
   cx<T> v[1][E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[0][m] = col[t * a.nx + m * rs];
-  const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[((long)inst * 2 + comp) * a.nx + kx];
+  for (int m = 0; m < E; ++m)
+    v[0][m] = in_bounds(a.flags, cbase + t * a.nx + m * rs, ctotal) ? col[t * a.nx + m * rs] : cx<T>{};
+  const long ai = ((long)inst * 2 + comp) * a.nx + kx;
+  const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[in_bounds(a.flags, ai, (long)a.ninst * 2 * a.nx) ? ai : 0];
   const T inv = col_inv<T>(a, inst * 2 + comp);
   col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, reinterpret_cast<const cx<T> *>(a.kyt), inv);
 #pragma unroll
-  for (int m = 0; m < E; ++m) col[t * a.nx + m * rs] = v[0][m];
+  for (int m = 0; m < E; ++m)
+    if (in_bounds(a.flags, cbase + t * a.nx + m * rs, ctotal)) col[t * a.nx + m * rs] = v[0][m];
 }
 
 // --------------------------------------------------------- energy passes

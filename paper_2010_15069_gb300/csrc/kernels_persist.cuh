@@ -66,8 +66,11 @@ __device__ __forceinline__ unsigned warp_partials_post(const RowArgs &a, int ins
   }
   unsigned prev = 0;
   if ((threadIdx.x & 31) == 0) {
-    a.partials[((long)inst * ngroups + group) * 2] = double(tsum[0]);
-    a.partials[((long)inst * ngroups + group) * 2 + 1] = double(tsum[1]);
+    if (in_bounds(a.flags, ((long)inst * ngroups + group) * 2 + 1, (long)a.ninst * a.ny * 2) &&
+        in_bounds(a.flags, inst, a.ninst)) {
+      a.partials[((long)inst * ngroups + group) * 2] = double(tsum[0]);
+      a.partials[((long)inst * ngroups + group) * 2 + 1] = double(tsum[1]);
+    }
     prev = count_group(&a.counters[inst]);
   }
   return prev;
@@ -163,6 +166,8 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
   auto issue = [&](int u) {
     const int inst = u / upi, y0 = (u - inst * upi) * RU;
     const cx<T> *src = reinterpret_cast<const cx<T> *>(a.psi) + ((long)inst * 2 * a.ny + y0) * N;
+    // (bounds-checked build: the last element of the second copy lies within psi)
+    in_bounds(a.flags, ((long)inst * 2 * a.ny + y0) * N + (long)a.ny * N + RU * N - 1, (long)a.ninst * 2 * a.ny * N);
     mbar_expect_tx(bar, 2 * CB);
     bulk_g2s(stage, src, CB, bar);
     bulk_g2s(stage + RU * N, src + (long)a.ny * N, CB, bar);
@@ -237,8 +242,10 @@ __global__ void __launch_bounds__(rowu_block(1 << LOGN, 1 << LOGE),
       else row_partials<T>(a, inst, group, upi, nsum);
     }
     cx<T> *p = reinterpret_cast<cx<T> *>(a.psi) + (((long)inst * 2 + comp) * a.ny + y) * N + t;
+    const long pb = (((long)inst * 2 + comp) * a.ny + y) * N + t, pt = (long)a.ninst * 2 * a.ny * N;
 #pragma unroll
-    for (int m = 0; m < E; ++m) p[m * TT] = v[0][m];
+    for (int m = 0; m < E; ++m)
+      if (in_bounds(a.flags, pb + m * TT, pt)) p[m * TT] = v[0][m];
     if constexpr ((F & F_PART) && U::WARP) warp_partials_finish<T>(a, inst, upi, prev);
     u = un;
   }
@@ -275,6 +282,9 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
   auto buf = [&](int s) { return reinterpret_cast<cx<T> *>(smem_raw + s * bufb); };
   auto issue = [&](int tile, int s) {
     const int pc = tile / cgroups, cg = tile - pc * cgroups;
+    // (bounds-checked build: the boxes lie within the tensor map)
+    in_bounds(a.flags, (long)(cg + 1) * C * XMUL - 1, (long)a.nx * XMUL);
+    in_bounds(a.flags, (long)pc * N + N - 1, (long)a.ninst * 2 * N);
     mbar_expect_tx(&bar[s], tilebytes);
     for (int h = 0; h < N; h += BOXH) tma_g2s_2d(buf(s) + h * C, &map, cg * C * XMUL, pc * N + h, &bar[s]);
   };
@@ -322,8 +332,10 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, btab, col_inv<T>(a, pc));
     cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + (long)pc * N * a.nx + kx;
     const int rs = TT * a.nx;
+    const long cb = (long)pc * N * a.nx + kx, ct = (long)a.ninst * 2 * N * a.nx;
 #pragma unroll
-    for (int m = 0; m < E; ++m) col[t * a.nx + m * rs] = v[0][m];
+    for (int m = 0; m < E; ++m)
+      if (in_bounds(a.flags, cb + t * a.nx + m * rs, ct)) col[t * a.nx + m * rs] = v[0][m];
     __syncthreads();  // every thread is done with buffer s
     // refill buffer s with the tile after the one waiting in the other buffer
     const int after = nxt < ntiles ? next_active(nxt + gridDim.x) : ntiles;
@@ -393,6 +405,9 @@ __global__ void __launch_bounds__(256, 2)
   };
   auto issue = [&](int tile, int s) {
     const int pc = tile / cgroups, cg = tile - pc * cgroups;
+    // (bounds-checked build: the box lies within the tensor map)
+    in_bounds(a.flags, (long)(cg + 1) * C - 1, a.nx);
+    in_bounds(a.flags, (long)pc * N + N - 1, (long)a.ninst * 2 * N);
     mbar_expect_tx(&bar[s], (uint32_t)kColW_Tile);
     tma_g2s_2d(tiles + s * kColW_Tile, &map, cg * C, pc * N, &bar[s]);
   };
@@ -442,6 +457,8 @@ __global__ void __launch_bounds__(256, 2)
     const int after = nxt < ntiles ? next_active(nxt + gridDim.x) : ntiles;
     if (threadIdx.x == 0) {
       const int cg = tile - pc * cgroups;
+      in_bounds(a.flags, (long)(cg + 1) * C - 1, a.nx);
+      in_bounds(a.flags, (long)pc * N + N - 1, (long)a.ninst * 2 * N);
       tma_s2g_2d(&map, cg * C, pc * N, tb);
       bulk_commit();
     }
