@@ -307,21 +307,111 @@ def oracle_fixed_point_residual(p, psi, dtau):
     return r
 
 
+WS_TRAIN, WS_ITERS, WS_BATCH, WS_LR, WS_SEED = 256, 1200, 4, 1e-3, 33
+
+
+def train_warm_start():
+    """The learned warm start (width 64, 32 modes, 4 Fourier layers, hidden
+    128): WS_TRAIN ground states of the sweep generator at 256^2 (parameters
+    from seed 33, disjoint from the timed instances' seed 3; vortex-seeded,
+    relaxed by the batched complex64 path with the lagged renormalisation to
+    residual 2e-3 or a stall), then WS_ITERS Adam steps on random batches of
+    WS_BATCH.  Everything runs on the default stream, in order with the
+    tensors it reads.  Returns (model, {seconds and losses})."""
+    import torch
+    import paper_2010_15069_gb300 as sp
+    from paper_2010_15069_gb300 import warmstart
+    n, L = 256, SWEEP_BOX
+    prm = inputs.sweep_params(WS_TRAIN, seed=WS_SEED)
+    grid = inputs.Grid(n, n, L, L)
+    info = {}
+    t0 = time.perf_counter()
+    with sp.Context(n, n, L, L, "c64", ninst=WS_TRAIN) as c:
+        for i, q in enumerate(prm):
+            p = inputs.problem(n, n, L, L, Omega=q["Omega"], delta_slope=q["delta_slope"], g11=q["g"], g22=q["g"],
+                               g12=q["g12"], kL=SWEEP_KL)
+            c.set_potentials_separable(i, **p.separable, g11=p.g11, g22=p.g22, g12=p.g12, kL=p.kL)
+        t = torch.from_numpy(np.stack([inputs.vortex_spinor(grid, n_vortices=20, radius=5.0, seed=5000 + i)
+                                       for i in range(WS_TRAIN)]).astype(np.complex64)).cuda()
+        c.relax(t, SWEEP_DTAU, 2e-3, 20000, TTR_CHECK, give_up=True, lagged=True)
+        gs = t.cpu().numpy().astype(np.complex128)
+    info["ground_states_s"] = time.perf_counter() - t0
+    feats = np.stack([warmstart.features(grid, q["g"], q["g12"], q["Omega"], q["delta_slope"]) for q in prm])
+    a = torch.from_numpy(feats).cuda()
+    y = torch.from_numpy(np.stack([warmstart.to_channels(x) for x in gs])).cuda()
+    f = sp.FNO(warmstart.CIN, warmstart.COUT, width=64, modes=32, layers=4, hidden=128, seed=1)
+    rng = np.random.default_rng(WS_SEED)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(WS_ITERS):
+        idx = torch.from_numpy(rng.choice(WS_TRAIN, WS_BATCH, replace=False)).cuda()
+        losses.append(f.train_step(a[idx].contiguous(), y[idx].contiguous(), WS_LR))
+    torch.cuda.synchronize()
+    info.update(train_s=time.perf_counter() - t0, iters=WS_ITERS, batch=WS_BATCH, samples=WS_TRAIN,
+                loss_first=float(np.mean(losses[:20])), loss_last=float(np.mean(losses[-20:])))
+    return f, info
+
+
+def warm_states(f, probs):
+    """The model's proposals for the given sweep problems, normalised to one
+    atom; (states, seconds including the host-side conversions)."""
+    import torch
+    from paper_2010_15069_gb300 import warmstart
+    prm = inputs.sweep_params(len(probs), seed=3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = []
+    for p, q in zip(probs, prm):
+        g = p.grid
+        a = torch.from_numpy(warmstart.features(g, q["g"], q["g12"], q["Omega"], q["delta_slope"])[None]).cuda()
+        psi = warmstart.from_channels(f.forward(a).cpu().numpy()[0])
+        nrm = g.dx * g.dy * float(np.sum(np.abs(psi) ** 2))
+        out.append(psi / np.sqrt(nrm) if nrm > 0 else psi)
+    return out, time.perf_counter() - t0
+
+
+def ground_state_verdict(psi_a, psi_b, e_a, e_b, res_a, res_b, tol, gap_est=0.1, e_tol=1e-5):
+    """The comparison of two relaxed ground states of the same problem
+    (metastable states may legitimately differ between two
+    runs): 'match' when both residuals are within tol and the states agree up
+    to the global phase within tol / gap_est (the distance to the fixed point
+    that a residual of tol allows for a slowest relaxation rate gap_est);
+    'degenerate' when the energies agree within e_tol (relative) but the
+    states do not (different metastable states of nearly equal energy, or a
+    run not below tol); 'mismatch' otherwise.  Returns (verdict, max |dpsi|
+    up to the phase, relative energy difference)."""
+    ph = np.vdot(psi_b, psi_a)
+    ph = ph / abs(ph) if abs(ph) > 0 else 1.0
+    dpsi = float(np.abs(psi_a - psi_b * ph).max())
+    de = abs(e_a - e_b) / max(abs(e_a), 1e-300)
+    if res_a <= tol and res_b <= tol and dpsi <= tol / gap_est:
+        return "match", dpsi, de
+    if de <= e_tol:
+        return "degenerate", dpsi, de
+    return "mismatch", dpsi, de
+
+
 def time_to_residual():
     """Wall time until the instances of one eighth of the sweep batch (8 x 256^2
-    + 2 x 512^2 + 1 x 1024^2, the headline's generator) reach residual 1e-8:
-    the plain FP64 path (one complex128 context per instance, one after
-    another, exact renormalisation) against the batched path (one multi-size
-    context: complex64 with the lagged renormalisation down to complex64's
-    rounding floor, then complex128, converged instances frozen).  Both arms
-    give up an instance whose best residual has not halved in 40 checks and
-    have the same step budget per instance (the batched arm's two stages
-    share it).  The time is charged over the instances both arms
+    + 2 x 512^2 + 1 x 1024^2, the headline's generator) reach residual 1e-8,
+    three ways:
+      plain: the plain FP64 path (one complex128 context per instance, one
+        after another, exact renormalisation, vortex-seeded);
+      batched: one multi-size context, complex64 with the lagged
+        renormalisation down to complex64's rounding floor, then complex128,
+        converged instances frozen (vortex-seeded);
+      warm: the same batched path started from the learned warm start's
+        proposals (inference and conversions timed with it; the training on
+        ground states of other parameter sets is reported apart).
+    Every arm gives up an instance whose best residual has not halved in 40
+    checks and has the same step budget per instance (the batched arms' two
+    stages share it).  Times are charged over the instances all arms
     converge: the plain arm's per-instance times summed over them, and a
-    second batched run of exactly those instances.  Per sampled converged
-    instance: the energy and max |dpsi| (up to the global phase) between the
-    two arms and the FP64 oracle's residual of one exact step from the batched
-    result."""
+    second run of exactly those instances for each batched arm.  Per sampled
+    converged instance: the energy and max |dpsi| (up to the global phase)
+    between the plain and the warm arm and the FP64 oracle's residual of one
+    exact step from the warm arm's result."""
     import torch
     import paper_2010_15069_gb300 as sp
     classes, probs, psi = sweep_problems(TTR_CLASSES)
@@ -339,9 +429,9 @@ def time_to_residual():
             plain.append({"res": float(res[0]), "steps": int(st[1]), "s": el, "psi": t.cpu().numpy(),
                           "energy": float(c.energy(t)[0, 0])})
 
-    def batched(idx):
+    def batched(idx, starts, extra_s=0.0):
         sub_probs = [probs[i] for i in idx]
-        sub_psi = [psi[i] for i in idx]
+        sub_psi = [starts[i] for i in idx]
         sub_classes = []
         for n, _ in TTR_CLASSES:
             k = sum(1 for p in sub_probs if p.grid.nx == n)
@@ -354,43 +444,66 @@ def time_to_residual():
             t0 = time.perf_counter()
             res, st = c.relax(flat, SWEEP_DTAU, TTR_TOL, TTR_MAX, TTR_CHECK, ladder=True, give_up=True,
                               lagged=True)
-            el = time.perf_counter() - t0
+            el = time.perf_counter() - t0 + extra_s
             en = c.energy(flat)[:, 0]
             views = [v.cpu().numpy() for v in c.class_views(flat)]
         states = [v[j] for v in views for j in range(v.shape[0])]
         return {"s": el, "res": res, "steps": st, "energy": en, "psi": states}
 
-    full = batched(list(range(B)))
-    both = [i for i in range(B) if plain[i]["res"] <= TTR_TOL and full["res"][i] <= TTR_TOL]
-    sub = full if len(both) == B else (batched(both) if both else None)
-    plain_s = sum(plain[i]["s"] for i in both)
+    cold = batched(list(range(B)), psi)
+    f, train_info = train_warm_start()
+    with f:
+        wpsi, infer_s = warm_states(f, probs)
+    if not all(np.isfinite(x).all() for x in wpsi):
+        raise RuntimeError("the warm-start network proposed a non-finite spinor")
+    warm = batched(list(range(B)), wpsi, infer_s)
+    conv = {"plain": [i for i in range(B) if plain[i]["res"] <= TTR_TOL],
+            "batched": [i for i in range(B) if cold["res"][i] <= TTR_TOL],
+            "warm": [i for i in range(B) if warm["res"][i] <= TTR_TOL]}
+    common = [i for i in range(B) if all(i in v for v in conv.values())]
+
+    def rerun(run_all, starts, extra):
+        if not common:
+            return None
+        if len(common) == B:
+            return run_all["s"]
+        return batched(common, starts, extra * len(common) / B)["s"]
+
+    plain_s = sum(plain[i]["s"] for i in common)
+    cold_s, warm_s = rerun(cold, psi, 0.0), rerun(warm, wpsi, infer_s)
     checks = []
-    for cls_n in sorted({probs[i].grid.nx for i in both}):
-        i = next(j for j in both if probs[j].grid.nx == cls_n)
-        a, b = plain[i]["psi"], full["psi"][i]
-        ph = np.vdot(b, a)
-        ph = ph / abs(ph) if abs(ph) > 0 else 1.0
-        checks.append({"instance": i, "grid": cls_n,
-                       "rel_energy_diff": abs(full["energy"][i] - plain[i]["energy"]) / abs(plain[i]["energy"]),
-                       "max_abs_dpsi_up_to_phase": float(np.abs(a - b * ph).max()),
-                       "oracle_one_step_residual": oracle_fixed_point_residual(probs[i], b, SWEEP_DTAU)})
+    for cls_n in sorted({probs[i].grid.nx for i in common}):
+        i = next(j for j in common if probs[j].grid.nx == cls_n)
+        verdict, dpsi, de = ground_state_verdict(plain[i]["psi"], warm["psi"][i], plain[i]["energy"],
+                                                 float(warm["energy"][i]), plain[i]["res"], float(warm["res"][i]),
+                                                 TTR_TOL)
+        checks.append({"instance": i, "grid": cls_n, "verdict_plain_vs_warm": verdict,
+                       "rel_energy_diff_plain_vs_warm": de, "max_abs_dpsi_plain_vs_warm_up_to_phase": dpsi,
+                       "oracle_one_step_residual": oracle_fixed_point_residual(probs[i], warm["psi"][i],
+                                                                                SWEEP_DTAU)})
+    verdicts = {}
+    for i in common:
+        v = ground_state_verdict(plain[i]["psi"], warm["psi"][i], plain[i]["energy"], float(warm["energy"][i]),
+                                 plain[i]["res"], float(warm["res"][i]), TTR_TOL)[0]
+        verdicts[v] = verdicts.get(v, 0) + 1
     return {"workload": "8 x 256^2 + 2 x 512^2 + 1 x 1024^2 instances of the sweep generator (seed 3), box "
-                        f"[-12,12]^2, kL=1, 20-vortex seeded, dtau={SWEEP_DTAU:g}, residual checked every "
-                        f"{TTR_CHECK} steps",
+                        f"[-12,12]^2, kL=1, dtau={SWEEP_DTAU:g}, residual checked every {TTR_CHECK} steps",
             "tol": TTR_TOL, "step_budget_per_instance": TTR_MAX,
-            "plain": "complex128, one context per instance in turn, exact renormalisation",
-            "batched": "one multi-size context: complex64 (lagged renormalisation) to its rounding floor, "
-                       "then complex128 (lagged), converged instances frozen",
-            "converged": {"plain": sum(pl["res"] <= TTR_TOL for pl in plain),
-                          "batched": int((full["res"] <= TTR_TOL).sum()), "both": len(both), "of": B},
-            "not_converged": {"plain": [i for i in range(B) if plain[i]["res"] > TTR_TOL],
-                              "batched": [i for i in range(B) if full["res"][i] > TTR_TOL]},
-            "plain_fp64_unbatched_s": plain_s, "batched_s": sub["s"] if sub else None,
-            "speedup": plain_s / sub["s"] if sub else None,
+            "arms": {"plain": "complex128, one context per instance in turn, exact renormalisation, 20-vortex seeded",
+                     "batched": "one multi-size context: complex64 (lagged renormalisation) to its rounding "
+                                "floor, then complex128 (lagged), converged instances frozen, 20-vortex seeded",
+                     "warm": "the batched path from the warm-start network's proposals (inference timed)"},
+            "converged": {k: len(v) for k, v in conv.items()} | {"all_arms": len(common), "of": B},
+            "not_converged": {k: [i for i in range(B) if i not in v] for k, v in conv.items()},
+            "seconds_over_common": {"plain_fp64_unbatched": plain_s, "batched": cold_s, "warm_batched": warm_s},
+            "speedup_over_plain": {"batched": plain_s / cold_s if cold_s else None,
+                                   "warm_batched": plain_s / warm_s if warm_s else None},
+            "warm_inference_s": infer_s, "warm_start_training": train_info,
             "plain_steps_per_instance": [pl["steps"] for pl in plain],
-            "batched_steps": {"complex64": int(full["steps"][0]), "complex128": int(full["steps"][1])},
-            "all_instances_s": {"plain": sum(pl["s"] for pl in plain), "batched": full["s"]},
-            "checks": checks}
+            "batched_steps": {"complex64": int(cold["steps"][0]), "complex128": int(cold["steps"][1])},
+            "warm_steps": {"complex64": int(warm["steps"][0]), "complex128": int(warm["steps"][1])},
+            "all_instances_s": {"plain": sum(pl["s"] for pl in plain), "batched": cold["s"], "warm": warm["s"]},
+            "verdicts_plain_vs_warm": verdicts, "checks": checks}
 
 
 # ------------------------------------------------------- single large instance
@@ -481,8 +594,11 @@ def fno_flops(n, cin=6, cout=4, W=64, M=32, L=4, H=128):
 def fno_throughput(n=256, batch=4, steps=10):
     """Training steps (forward, backward, Adam) of the warm-start FNO at its full
     size (width 64, 32 modes, 4 layers, 67.1 M parameters) on n x n inputs:
-    samples/s and the achieved FP32 rate (training = 3 forward passes) against
-    the FP32 FMA peak of the CUDA cores at the sampled clock."""
+    samples/s and the achieved rate of the network's algorithmic flops (training
+    = 3 forward passes).  The pointwise channel products and the weight
+    gradients run on the tcgen05 tensor cores (float32 operands split into
+    bfloat16 terms: three MMA passes each); the truncated-DFT contractions
+    and the per-mode mixing run on the CUDA cores."""
     import torch
     import paper_2010_15069_gb300 as sp
     rng = np.random.default_rng(0)
@@ -502,7 +618,9 @@ def fno_throughput(n=256, batch=4, steps=10):
     return {"workload": f"FNO width 64, 32 modes, 4 layers, hidden 128 (67.1 M parameters), {n}x{n}, batch {batch}, "
                         "bfloat16 weights, FP32 accumulate, one Adam step per batch",
             "ms_per_train_step": sec * 1e3, "samples_per_s": batch / sec,
-            "achieved_tflops": flop / sec / 1e12, "bound": "alu"}
+            "achieved_tflops": flop / sec / 1e12,
+            "where": "channel products and weight gradients on tcgen05 tensor cores; truncated DFTs and mode "
+                     "mixing on CUDA cores"}
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -630,6 +748,15 @@ def measured_traffic(key):
 def torch_sm_count():
     import torch
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def bf16_peaks():
+    """The sustained dense bfloat16 rate of MEASURED_PEAKS.json (TFLOP/s), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def peaks():
@@ -893,17 +1020,25 @@ def run_fused(args):
     }
     if rt is not None:
         line["realtime_batch"] = rt
+    # the secondary measurements: a failure in one is recorded in its place
+    def secondary(fn):
+        try:
+            return fn()
+        except Exception as e:  # noqa: BLE001 - the headline line is printed regardless
+            log(f"secondary measurement failed: {e!r}")
+            return {"error": repr(e)}
     if world == 1 and args.ttr:
-        line["time_to_residual"] = time_to_residual()
+        line["time_to_residual"] = secondary(time_to_residual)
     if world == 1 and args.single:
-        line["single_instance"] = single_instance(args.single_steps, tune=args.schedule == "auto")
+        line["single_instance"] = secondary(lambda: single_instance(args.single_steps, tune=args.schedule == "auto"))
     if world == 1 and args.fno:
         fn = fno_throughput()
-        sm = line["clocks"].get("sm_mhz") or 2070.0
-        # FP32 FMA peak of the CUDA cores: SMs x 128 lanes x 2 flop x clock
-        fpk = torch_sm_count() * 128 * 2 * sm * 1e6 / 1e12
-        fn.update(peak_tflops=fpk, frac=fn["achieved_tflops"] / fpk,
-                  peak_source="derived: SMs x 128 FP32 lanes x 2 x sampled SM clock")
+        bf16 = bf16_peaks()
+        fp32 = ceil.get("fp32_fma_tflops") if isinstance(ceil, dict) else None
+        fn.update(frac_of_bf16_tensor_sustained=fn["achieved_tflops"] / bf16 if bf16 else None,
+                  bf16_tensor_sustained_tflops=bf16,
+                  frac_of_fp32_fma=fn["achieved_tflops"] / fp32 if fp32 else None, fp32_fma_tflops=fp32,
+                  peak_source="MEASURED_PEAKS.json bf16_tflops_sustained; FP32 fma from spgpe_probe_ceilings")
         line["warm_start_fno"] = fn
     print(json.dumps(line), flush=True)
     if dist is not None:

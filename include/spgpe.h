@@ -360,10 +360,12 @@ int spgpe_probe_ceilings(double *out, int n_out);
  * no counterpart: this serves callers that cannot call cudaMalloc, such as
  * host applications or plugins that hand out all device memory from their own
  * pool, or that run under a fixed device-memory budget where a library may not
- * allocate).  No context is needed and nothing is allocated, on the device or
- * the host: the partial sums live in a 256 KiB array of device memory that is
- * part of the library and that every GPU loading it keeps until the process
- * exits.  psi is the caller's device buffer [ninst][2][ny][nx] complex of the
+ * allocate).  No context is needed and the call allocates nothing, on the
+ * device or the host: the partial sums live in a 256 KiB array of device
+ * memory that is part of the library's device code.  The CUDA runtime
+ * reserves that array on a GPU when it loads the library's module there (with
+ * lazy module loading, possibly during the first call), and the GPU keeps it
+ * until the process exits.  psi is the caller's device buffer [ninst][2][ny][nx] complex of the
  * given dtype (SPGPE_C64 or SPGPE_C128) over [-xmax, xmax) x [-ymax, ymax);
  * out is a host array of 2*ninst doubles receiving {N_up, N_dn} per instance
  * (dx dy sum |psi_j|^2, FP64 accumulation).  Runs on cuda_stream (a

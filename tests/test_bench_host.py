@@ -34,3 +34,19 @@ def test_oracle_pool_uses_every_core(orc):
     expect = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     assert cores == expect
     assert rate > 0 and wall > 0.3
+
+
+def test_ground_state_verdict():
+    """two relaxed states of one problem 'match' when both are
+    converged and agree up to the global phase, are 'degenerate' when only
+    their energies agree, and a 'mismatch' otherwise."""
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((2, 8, 8)) + 1j * rng.standard_normal((2, 8, 8))
+    b = a * np.exp(0.7j)  # the same state, another global phase
+    assert bench.ground_state_verdict(a, b, 1.0, 1.0, 1e-9, 1e-9, 1e-8)[0] == "match"
+    c = a + 1e-3 * rng.standard_normal(a.shape)
+    assert bench.ground_state_verdict(a, c, 1.0, 1.0 + 1e-7, 1e-9, 1e-9, 1e-8)[0] == "degenerate"
+    assert bench.ground_state_verdict(a, b, 1.0, 1.0, 1e-9, 1e-6, 1e-8)[0] == "degenerate"  # b not converged
+    assert bench.ground_state_verdict(a, c, 1.0, 1.01, 1e-9, 1e-9, 1e-8)[0] == "mismatch"
