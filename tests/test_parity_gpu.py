@@ -378,6 +378,28 @@ def test_bench_workload_sampled_instances(orc, ground0):
         assert np.abs(got[k] - ref).max() < 1e-4, i
 
 
+def test_largest_grid_2048_c64_error_growth(orc):
+    """2048^2 real time (config 4's grid: box [-24,24]^2, dt = 5e-4, trap
+    quenched to omega = 1.1, Raman coupling, detuning gradient, SOC, g = 1000,
+    g12 = 900) from a 20-vortex seeded state: complex64 against the oracle
+    after 50, 100, 150 and 200 steps (the error growth of complex64 at this
+    size; bar 1e-4 per the complex64 tolerance)."""
+    p = inputs.problem(2048, 2048, 24.0, 24.0, omega=1.1, Omega=2.0, delta_slope=0.2, g11=1000.0, g22=1000.0,
+                       g12=900.0, kL=1.0)
+    psi = inputs.vortex_spinor(p.grid, n_vortices=20, radius=6.0, seed=4)
+    m = model_for(orc, p)
+    errs = []
+    with ctx_for(p, "c64", separable=True) as c:
+        t = to_dev(psi, "c64")
+        ref = psi
+        for _ in range(4):
+            c.step_real(t, 5e-4, 50)
+            ref = m.step(ref, 5e-4, 50)
+            errs.append(float(np.abs(to_host(t) - ref).max()))
+    print("2048^2 complex64 max|dpsi| after 50/100/150/200 steps:", errs)
+    assert all(e < 1e-4 for e in errs), errs
+
+
 def test_largest_grid_2048_c64(orc):
     """2048^2 real time (box [-24,24]^2, dt = 5e-4): three steps against the oracle."""
     p = inputs.problem(2048, 2048, 24.0, 24.0, Omega=2.0, delta_slope=0.2, g11=1000.0, g22=1000.0,
