@@ -12,8 +12,9 @@
 // another in registers with no shared-memory round trip in between; only the
 // S-1 inner stage boundaries of each transform go through shared memory.
 //
-// Radix plan: S = ceil(LOGN / LOGE) stages, log2 radices split as evenly as
-// possible (2048 = 16*16*8 at E = 16, 256 = 16*16, 64 = 8*8, ...).
+// Radix plan: S = max(ceil(LOGN / LOGE), ceil(LOGN / 4)) stages (radices of
+// at most 16), log2 radices split as evenly as possible (2048 = 16*16*8 at
+// E = 16, 256 = 16*16, 64 = 8*8, 512 = 8*8*8 at E = 32, ...).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -163,7 +164,7 @@ __device__ __forceinline__ void dft(cx<T> (&v)[R]) {
 // Stage plan of a 2^LOGN transform with 2^LOGE elements per thread.
 template <int LOGN, int LOGE>
 struct Plan {
-  static constexpr int S = (LOGN + LOGE - 1) / LOGE;
+  static constexpr int S = (LOGN + LOGE - 1) / LOGE > (LOGN + 3) / 4 ? (LOGN + LOGE - 1) / LOGE : (LOGN + 3) / 4;
   __host__ __device__ static constexpr int bits(int s) { return LOGN / S + (s < LOGN % S ? 1 : 0); }
   __host__ __device__ static constexpr int nsbits(int s) { return s == 0 ? 0 : nsbits(s - 1) + bits(s - 1); }
   // offset of stage s in the twiddle table (stage 0 has none)

@@ -2,14 +2,16 @@
 // fft_core.cuh), computed in FP64 and rounded once to the working precision
 // when uploaded.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 namespace spgpe {
 
 // Twiddle table of the block FFT plan for n = 2^logn points with 2^loge
-// values per thread (the plan of fft_core.cuh: S = ceil(logn / loge) stages,
-// radix bits split as evenly as possible, larger first).  Stage s >= 1 holds
+// values per thread (the plan of fft_core.cuh: S = max(ceil(logn / loge),
+// ceil(logn / 4)) stages, radix bits split as evenly as possible, larger
+// first).  Stage s >= 1 holds
 // entries [r - 1][k], r = 1..R-1, k = 0..NS-1, for the root exp(-2 pi i m / n),
 // m = r k n / (NS R); 16 bytes per entry:
 //   complex64:  (tan(phi/2), sin(phi), g, g) with exp(-2 pi i m / n) = g e^{i phi},
@@ -18,7 +20,7 @@ namespace spgpe {
 inline std::vector<double> stage_twiddles(int logn, int loge, bool single) {
   const double kTwoPi = 6.28318530717958647692528676655900577;
   const int n = 1 << logn;
-  const int S = (logn + loge - 1) / loge;
+  const int S = std::max((logn + loge - 1) / loge, (logn + 3) / 4);
   std::vector<double> out;
   int ns = 1;
   for (int s = 0; s < S; ++s) {

@@ -3,7 +3,7 @@
 The device transform reads stage s's entry (r, k) at Plan::off(s) + (r-1) NS + k
 with compile-time offsets; the host builds the table separately.  A small
 program compiled against both (fft_core.cuh's Plan, twiddles.h's builder)
-checks, for every plan the library can use (8 to 4096 points, 4 to 16 values
+checks, for every plan the library can use (8 to 4096 points, 4 to 32 values
 per thread, both precisions), that the table has exactly Plan::entries()
 entries and that every entry decodes to the root the plan expects at that
 position: exp(-2 pi i r k / (NS R)), from the DFT's definition.
@@ -66,7 +66,7 @@ template <int LOGE, int... L> int all(std::integer_sequence<int, L...>) { return
 
 int main() {
   const int bad = all<2>(std::make_integer_sequence<int, 10>{}) + all<3>(std::make_integer_sequence<int, 10>{}) +
-                  all<4>(std::make_integer_sequence<int, 10>{});
+                  all<4>(std::make_integer_sequence<int, 10>{}) + all<5>(std::make_integer_sequence<int, 10>{});
   printf("%d mismatches\n", bad);
   return bad != 0;
 }
