@@ -307,17 +307,18 @@ def oracle_fixed_point_residual(p, psi, dtau):
     return r
 
 
-WS_TRAIN, WS_ITERS, WS_BATCH, WS_LR, WS_SEED = 256, 1200, 4, 1e-3, 33
+WS_TRAIN, WS_ITERS, WS_BATCH, WS_LR, WS_SEED = 256, 1500, 4, 1e-3, 33
 
 
 def train_warm_start():
     """The learned warm start (width 64, 32 modes, 4 Fourier layers, hidden
     128): WS_TRAIN ground states of the sweep generator at 256^2 (parameters
-    from seed 33, disjoint from the timed instances' seed 3; vortex-seeded,
-    relaxed by the batched complex64 path with the lagged renormalisation to
-    residual 2e-3 or a stall), then WS_ITERS Adam steps on random batches of
-    WS_BATCH.  Everything runs on the default stream, in order with the
-    tensors it reads.  Returns (model, {seconds and losses})."""
+    from seed 33, disjoint from the timed instances' seed 3), relaxed by the
+    batched complex64 path with the lagged renormalisation to residual 2e-3 or
+    a stall from 20-vortex seeded spinors (the seeding the timed arms use),
+    then WS_ITERS Adam steps on random batches of WS_BATCH.  Everything runs
+    on the default stream, in order with the tensors it reads.  Returns
+    (model, {seconds and losses})."""
     import torch
     import paper_2010_15069_gb300 as sp
     from paper_2010_15069_gb300 import warmstart
