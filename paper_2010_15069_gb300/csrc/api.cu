@@ -263,11 +263,13 @@ int upload_raw(spgpe_ctx *c) {
 }
 
 // Step tables for substep dt (real or imaginary time):
-//   x/y step tables {V + delta/2, V - delta/2, X constants} of the separable
-//   pieces (imaginary time: exp(-(dt/2) (V +- delta/2)), the potential
-//   factors of D(dt/2), which multiply to the factor of the sum), X constants for the angle a = Omega_piece dt / 8 of X(dt/4):
-//   (tan(a/2), sin a) in real time (three-shear rotation), (cosh a - 1,
-//   sinh a) in imaginary time (to full relative precision);
+//   x/y step tables {p(V + delta/2), p(V - delta/2), X constants} of the
+//   separable pieces: p(v) = -(dt/4) v, the half phase of D(dt/2), in real
+//   time; p(v) = exp(-(dt/2) v), the potential factors of D(dt/2), which
+//   multiply to the factor of the sum, in imaginary time.  X constants for
+//   the angle a = Omega_piece dt / 8 of X(dt/4), each applied as three shears:
+//   (tan(a/2), sin a) of the rotation in real time, (tanh(a/2), sinh a) of
+//   the hyperbolic rotation in imaginary time;
 //   K tables a_j(kx) - 1 with a_j = exp(-i dt (kx^2/2 -+ kL kx)) and b(ky) - 1
 //   with b = exp(-i dt ky^2/2) (imaginary time: exp(-dt (...)) - 1); the
 //   1/(nx ny) of the inverse transform is applied in the kernel.
@@ -278,8 +280,7 @@ int ensure_tables(spgpe_ctx *c, double dt, int imag) {
   bool too_big = false;
   auto rot = [&](double ang, double &mm, double &ss) {
     if (imag) {
-      const double sh = std::sinh(0.5 * ang);
-      mm = 2.0 * sh * sh;
+      mm = std::tanh(0.5 * ang);
       ss = std::sinh(ang);
     } else {
       if (std::fabs(ang) > 0.25 * kTwoPi) too_big = true;
@@ -298,9 +299,10 @@ int ensure_tables(spgpe_ctx *c, double dt, int imag) {
       o[1] = -std::sin(th);
     }
   };
-  // potential entries: V +- delta/2 (real time), or the factors
-  // exp(-(dt/2) (V +- delta/2)) of D(dt/2) in imaginary time
-  auto pot = [&](double v) { return imag ? std::exp(-0.5 * dt * v) : v; };
+  // potential entries: htau (V +- delta/2) with htau = -dt/4, the half phase
+  // of D(dt/2) (real time), or the factors exp(-(dt/2) (V +- delta/2)) of
+  // D(dt/2) in imaginary time
+  auto pot = [&](double v) { return imag ? std::exp(-0.5 * dt * v) : -0.25 * dt * v; };
   for (int i = 0; i < ni; ++i) {
     for (int x = 0; x < nx; ++x) {
       const double *h = &c->hx[((size_t)i * nx + x) * 3];

@@ -35,8 +35,10 @@ constexpr int kImagLag = F_IMAG | F_IFFT | F_REND | F_PART | F_LAG | F_RSTART | 
 // Arguments of the fused row pass (x direction, both components per thread).
 struct RowArgs {
   void *psi;              // [ninst][2][ny][nx] complex, in place
-  const void *tabx;       // [ninst][nx] {Vx+dx/2, Vx-dx/2, X constants} step table
-  const void *taby;       // [ninst][ny] {Vy+dy/2, Vy-dy/2, X constants} step table
+  // step tables [ninst][nx], [ninst][ny]: {p(V+delta/2), p(V-delta/2), X constants}
+  // of the separable pieces, p(v) = htau v (real time) or exp(-(dt/2) v)
+  const void *tabx;
+  const void *taby;
                           // (imaginary time: the factors exp(-tau (V +- delta/2)) of the
                           // separable pieces in place of the potentials)
                           // X constants: (tan(a/2), sin a) in real time, (cosh a - 1, sinh a)

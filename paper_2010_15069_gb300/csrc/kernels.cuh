@@ -30,53 +30,49 @@ struct alignas(4 * sizeof(T)) q4 {
 
 // ------------------------------------------------------------ math helpers
 
-// Every unit-modulus factor of the step (the D phase, the Raman rotation X,
-// the kinetic factor K) is applied as z + (f - 1) z with f - 1 evaluated to
-// full relative precision (f - 1 = -2 sin^2(h) + 2i sin(h) cos(h), h the half
-// phase; expm1 in imaginary time).  Multiplying by a rounded (cos, sin) pair
-// instead would change |z| by a fixed, phase-dependent amount each step; those
-// errors are systematic for slowly varying phases and add up over thousands
-// of steps.  The operations are written with explicit fma so that every
-// kernel that applies them rounds identically.
+// No factor of the step may change |psi| by a fixed, rounding-made amount
+// each time it is applied: such errors are systematic for slowly varying
+// phases and add up over thousands of steps.  So the kinetic factor K is
+// applied as z + (f - 1) z with f - 1 evaluated to full relative precision
+// (f - 1 = -2 sin^2(h) + 2i sin(h) cos(h), h the half phase; expm1 in
+// imaginary time), the small part first and z added last; the real-time D
+// phase and the Raman rotation X (in imaginary time the hyperbolic rotation)
+// are three-shear rotations, whose determinant is one whatever the rounding
+// of their constants.  The operations are written with explicit fma so that
+// every kernel that applies them rounds identically.
 
-// (cos(a) - 1, sin(a)) of a rotation angle, or (cosh(a) - 1, sinh(a)), to full
-// relative precision: cosh(a) - 1 = 2 sinh^2(a/2), sinh(b) = (expm1(b) - expm1(-b))/2.
-template <bool IMAG, class T> __device__ __forceinline__ void rot_of(T ang, T &m, T &s) {
-  if constexpr (IMAG) {
-    const T hh = T(0.5) * (expm1_f(T(0.5) * ang) - expm1_f(T(-0.5) * ang));
-    m = T(2) * hh * hh;
-    s = T(0.5) * (expm1_f(ang) - expm1_f(-ang));
+// Shear constants (tanh(a/2), sinh a) of the hyperbolic rotation by a (the
+// imaginary-time X of a 2D Omega entry), from expm1 to full relative
+// precision: tanh(a/2) = e / (e + 2) and sinh a = (e - expm1(-a)) / 2 with
+// e = expm1(a).
+template <class T> __device__ __forceinline__ void hrot_consts(T a, T &t, T &s) {
+  if constexpr (sizeof(T) == 4) {
+    const T e = expm1_f(a), f = expm1_f(-a);
+    t = e / (e + T(2));
+    s = T(0.5) * (e - f);
   } else {
-    expi2_m1(T(0.5) * ang, m, s);
+    t = tanh(T(0.5) * a);
+    s = sinh(a);
   }
 }
 
-// Angle addition in the (c - 1, s) representation.
-template <bool IMAG, class T> __device__ __forceinline__ void rot_compose(T &m, T &s, T m2, T s2) {
-  const T nm = d_fma(m, m2, d_fma(IMAG ? s : -s, s2, m + m2));
-  const T ns = d_fma(s, m2, d_fma(s2, m, s + s2));
-  m = nm;
-  s = ns;
+// Imaginary-time X(theta) = exp(-theta sigma_x): the hyperbolic rotation
+// [[cosh, -sinh], [-sinh, cosh]] of the planes (Re u, Re d) and (Im u, Im d),
+// each as three shears x -= t y; y -= s x; x -= t y with t = tanh(theta/2),
+// s = sinh(theta) (their product is [[1 + t s, -t (2 + t s)], [-s, 1 + t s]]
+// and 1 + t s = cosh theta); 6 fma, determinant one.
+template <class T> __device__ __forceinline__ void opXh(cx<T> &u, cx<T> &d, T t, T s) {
+  const T x1 = d_fma(-t, d.re, u.re);
+  const T y1 = d_fma(-s, x1, d.re);
+  const T x2 = d_fma(-t, y1, x1);
+  const T p1 = d_fma(-t, d.im, u.im);
+  const T q1 = d_fma(-s, p1, d.im);
+  const T p2 = d_fma(-t, q1, p1);
+  u = {x2, p2};
+  d = {y1, q1};
 }
 
-// X: (u, d) <- exp(-i theta sigma_x) (u, d) with (m, s) = (cos theta - 1, sin theta);
-// imaginary time exp(-theta sigma_x) with (cosh theta - 1, sinh theta).
-// Each output is a + (m a + s b'): the small terms are summed first and the
-// large one added last, so the second-order term m a (often below half an
-// ulp of a) is not rounded away.  Dropping it would leave |X|^2 = 1 + s^2 and
-// grow the atom number by s^2 at every application.
-template <bool IMAG, class T> __device__ __forceinline__ void opX(cx<T> &u, cx<T> &d, T m, T s) {
-  const cx<T> a = u, b = d;
-  if constexpr (IMAG) {
-    u = {a.re + d_fma(m, a.re, -s * b.re), a.im + d_fma(m, a.im, -s * b.im)};
-    d = {b.re + d_fma(m, b.re, -s * a.re), b.im + d_fma(m, b.im, -s * a.im)};
-  } else {
-    u = {a.re + d_fma(m, a.re, s * b.im), a.im + d_fma(m, a.im, -s * b.re)};
-    d = {b.re + d_fma(m, b.re, s * a.im), b.im + d_fma(m, b.im, -s * a.re)};
-  }
-}
-
-// z <- z + z w for a complex w = f - 1 (small part first, as in opX).
+// z <- z + z w for a complex w = f - 1 (small part first, z added last).
 template <class T> __device__ __forceinline__ cx<T> add_mul1(cx<T> z, cx<T> w) {
   return {z.re + d_fma(z.re, w.re, -(z.im * w.im)), z.im + d_fma(z.re, w.im, z.im * w.re)};
 }
@@ -88,24 +84,30 @@ static __device__ __noinline__ float expm1_general(float x) { return expm1_f(x);
 __device__ __forceinline__ double expm1_general(double x) { return expm1(x); }
 
 // D(tau): diagonal potential + mean-field phase (decay), densities on entry.
-// htau = -tau/2 in real time (the half phase), -tau in imaginary time.
-// Real time: vu, vd are V +- delta/2 and the phase is the whole exponent.
+// htau = -tau/2 in real time (the half phase), -tau in imaginary time; the
+// couplings arrive multiplied by it (gh11 = htau g11, ...: per instance, formed
+// once by the caller).
+// Real time: vu, vd are htau (V +- delta/2), so that the half phase is
+// h = vu + gh11 rho_up + gh12 rho_dn (resp. down), the whole exponent.
 // Imaginary time: vu, vd are the potential factors exp(-tau (V +- delta/2))
 // (from the step tables) and only the interaction exponent -tau (g11 rho_up +
 // g12 rho_dn) (resp. down) goes through expm1: exp(-tau (V + g rho)) =
 // exp(-tau V) (1 + expm1(-tau g rho)).
-// TIER (the caller has checked it for every point of the warp): 0: |htau e|
-// < 1/64, 1: |htau e| < 1/8 (imaginary time: < 1/2, e the interaction part),
-// so the series need no range reduction; 2: any phase.  FP64 always takes the
-// library functions.
+// TIER (the caller has checked it for every point of the warp): real time
+// 0: |h| < 1/64, 1: |h| < 1/8; imaginary time (h the interaction exponent)
+// 0: |h| < 1/4, 1: |h| < 1/2; so the series need no range reduction; 2: any
+// phase.  FP64 always takes the library functions.
 template <bool IMAG, int TIER = 2, class T>
-__device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22, T g12, T htau) {
+__device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T gh11, T gh22, T gh12) {
   constexpr bool F32 = sizeof(T) == 4;
   const T ru = d_fma(u.re, u.re, u.im * u.im), rd = d_fma(d.re, d.re, d.im * d.im);
   if constexpr (IMAG) {
-    const T hu = htau * d_fma(g12, rd, g11 * ru), hd = htau * d_fma(g12, ru, g22 * rd);
+    const T hu = d_fma(gh12, rd, gh11 * ru), hd = d_fma(gh12, ru, gh22 * rd);
     T fu, fd;
-    if constexpr (F32 && TIER < 2) {
+    if constexpr (F32 && TIER == 0) {
+      fu = expm1_quarter(hu);
+      fd = expm1_quarter(hd);
+    } else if constexpr (F32 && TIER == 1) {
       fu = expm1_small(hu);
       fd = expm1_small(hd);
     } else {
@@ -116,10 +118,9 @@ __device__ __forceinline__ void opD(cx<T> &u, cx<T> &d, T vu, T vd, T g11, T g22
     u = {u.re * au, u.im * au};
     d = {d.re * ad, d.im * ad};
   } else {
-    const T eu = d_fma(g12, rd, d_fma(g11, ru, vu));
-    const T ed = d_fma(g12, ru, d_fma(g22, rd, vd));
-    const T hu = htau * eu, hd = htau * ed;
-    // the phases exp(-i tau e) as three-shear rotations by 2 h, h = htau e
+    const T hu = d_fma(gh12, rd, d_fma(gh11, ru, vu));
+    const T hd = d_fma(gh12, ru, d_fma(gh22, rd, vd));
+    // the phases exp(-i tau e) as three-shear rotations by 2 h
     // (determinant one: no systematic change of |psi| from rounded constants)
     T tu, su, td, sd;
     if constexpr (F32 && TIER == 0) {
@@ -155,30 +156,29 @@ template <class T> __device__ __forceinline__ void opXr(cx<T> &u, cx<T> &d, T t,
   d = {q1, y1};
 }
 
-// X constants at one point.  Imaginary time: (cosh - 1, sinh) of the summed
-// angle.  Real time: the separate rotations of the y piece, the x piece and
-// the 2D piece of the angle (rotations about sigma_x commute), each applied
-// only when that piece is present.
+// X constants at one point: the separate rotations of the y piece, the x
+// piece and the 2D piece of the angle (rotations about sigma_x commute), each
+// applied only when that piece is present; (tan, sin) of the half and whole
+// angle in real time, (tanh, sinh) in imaginary time.
 template <class T> struct XPoint {
-  T m, s;          // imaginary time: composed (cosh - 1, sinh); real time: y piece (tan, sin)
-  T tx, sx;        // real time: x piece
-  T t2, s2;        // real time: 2D piece
-  bool n2;         // 2D piece rotates by 2r + pi: negate afterwards
+  T m, s;          // y piece
+  T tx, sx;        // x piece
+  T t2, s2;        // 2D piece
+  bool n2;         // real time: the 2D piece rotates by 2r + pi, negate afterwards
 };
 
 template <bool IMAG, class T>
 __device__ __forceinline__ void applyX(cx<T> &u, cx<T> &d, const XPoint<T> &x, int pieces) {
-  if constexpr (IMAG) {
-    opX<true>(u, d, x.m, x.s);
-  } else {
-    if (pieces & 1) opXr(u, d, x.m, x.s);
-    if (pieces & 2) opXr(u, d, x.tx, x.sx);
-    if (pieces & 4) {
-      opXr(u, d, x.t2, x.s2);
-      if (x.n2) {
-        u = {-u.re, -u.im};
-        d = {-d.re, -d.im};
-      }
+  auto rot = [&](T t, T s) {
+    if constexpr (IMAG) opXh(u, d, t, s); else opXr(u, d, t, s);
+  };
+  if (pieces & 1) rot(x.m, x.s);
+  if (pieces & 2) rot(x.tx, x.sx);
+  if (pieces & 4) {
+    rot(x.t2, x.s2);
+    if (!IMAG && x.n2) {
+      u = {-u.re, -u.im};
+      d = {-d.re, -d.im};
     }
   }
 }
@@ -223,22 +223,15 @@ template <class T> __device__ __forceinline__ bool x_double(T t, T s, T &tm, T &
 template <bool IMAG, class T>
 __device__ __forceinline__ XPoint<T> xpoint(const q4<T> &px, const q4<T> &ty, bool has2d, T q2z, T xang) {
   XPoint<T> r;
-  if constexpr (IMAG) {
-    r.m = px.z;
-    r.s = px.w;
-    rot_compose<true>(r.m, r.s, ty.z, ty.w);
-    if (has2d) {
-      T m2, s2;
-      rot_of<true>(q2z * xang, m2, s2);
-      rot_compose<true>(r.m, r.s, m2, s2);
-    }
-  } else {
-    r.m = ty.z;
-    r.s = ty.w;
-    r.tx = px.z;
-    r.sx = px.w;
-    r.n2 = false;
-    if (has2d) shear_consts_2h(T(0.5) * q2z * xang, r.t2, r.s2, r.n2);
+  r.m = ty.z;
+  r.s = ty.w;
+  r.tx = px.z;
+  r.sx = px.w;
+  r.t2 = r.s2 = T(0);
+  r.n2 = false;
+  if (has2d) {
+    if constexpr (IMAG) hrot_consts(q2z * xang, r.t2, r.s2);
+    else shear_consts_2h(T(0.5) * q2z * xang, r.t2, r.s2, r.n2);
   }
   return r;
 }
@@ -320,18 +313,26 @@ template <class T, int C> struct ColAccC {
 // their values with shuffles: the up-thread then owns positions m < E/2 of
 // both components, the down-thread positions m >= E/2; they swap back after.
 
-// R_end and/or R_start at this thread's H points (both components).
+// R_end and/or R_start at one point x of row y (both components).
 // MERGE (the fused real-time pass): X D X X D X with the middle X X as one
 // doubled X (exact: the two factors are the same rotation about sigma_x).
 // TIER: the phase tier of opD, one instantiation per tier so that each warp
-// runs straight-line code.
-// R_end and/or R_start at one point x of row y (both components).
-template <class T, int N, int F, int TIER>
+// runs straight-line code.  SIMPLE: the common layout, fixed at compile time
+// so that no point tests it: no 2D potential table, the Raman rotation in the
+// y piece only (an absent rotation is the exact identity), and in real time
+// the doubled y rotation valid (ymerge).  gh11, gh22, gh12 are the couplings
+// times htau; the real-time step tables hold htau (V +- delta/2).
+template <class T, int N, int F, int TIER, bool SIMPLE>
 __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4<T> *tab, const q4<T> &ty,
-                                      const q4<T> *p2, T g11, T g22, T g12, T htau, T xang, int pieces, bool ymerge,
-                                      T tm, T sm, T su, T sd, T (&nsum)[2]) {
+                                      const q4<T> *p2, T gh11, T gh22, T gh12, T htau, T xang, int pieces,
+                                      bool ymerge, T tm, T sm, T su, T sd, T (&nsum)[2]) {
   constexpr bool IMAG = (F & F_IMAG) != 0;
   constexpr bool MERGE = !IMAG && (F & F_REND) && (F & F_RSTART) && !(F & F_PART);
+  if constexpr (SIMPLE) {
+    p2 = nullptr;
+    pieces = 1;
+    ymerge = true;
+  }
   const q4<T> px = tab[x];
   T vu, vd, q2z = T(0);
   if constexpr (IMAG) {  // potential factors exp(-tau (V +- delta/2)) of the separable pieces
@@ -347,22 +348,22 @@ __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4
       vu *= exp(htau * q.x);
       vd *= exp(htau * q.y);
     } else {
-      vu += q.x;
-      vd += q.y;
+      vu = d_fma(htau, q.x, vu);
+      vd = d_fma(htau, q.y, vd);
     }
     q2z = q.z;
   }
   const XPoint<T> xc = xpoint<IMAG, T>(px, ty, p2 != nullptr, q2z, xang);
   if constexpr (MERGE) {
     applyX<false>(u, d, xc, pieces);
-    opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+    opD<false, TIER>(u, d, vu, vd, gh11, gh22, gh12);
     applyX2(u, d, xc, pieces, ymerge, tm, sm);
-    opD<false, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+    opD<false, TIER>(u, d, vu, vd, gh11, gh22, gh12);
     applyX<false>(u, d, xc, pieces);
   } else {
     if constexpr (F & F_REND) {
       applyX<IMAG>(u, d, xc, pieces);
-      opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+      opD<IMAG, TIER>(u, d, vu, vd, gh11, gh22, gh12);
       applyX<IMAG>(u, d, xc, pieces);
     }
     if constexpr (F & F_PART) {
@@ -375,27 +376,23 @@ __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4
     }
     if constexpr (F & F_RSTART) {
       applyX<IMAG>(u, d, xc, pieces);
-      opD<IMAG, TIER>(u, d, vu, vd, g11, g22, g12, htau);
+      opD<IMAG, TIER>(u, d, vu, vd, gh11, gh22, gh12);
       applyX<IMAG>(u, d, xc, pieces);
     }
   }
 }
 
-// R_end and/or R_start at this thread's H points (both components).
-// MERGE (the fused real-time pass): X D X X D X with the middle X X as one
-// doubled X (exact: the two factors are the same rotation about sigma_x).
-// TIER: the phase tier of opD, one instantiation per tier so that each warp
-// runs straight-line code.
-template <class T, int LOGN, int LOGE, int F, int TIER>
+// R_end and/or R_start at this thread's H points (both components), as r_one.
+template <class T, int LOGN, int LOGE, int F, int TIER, bool SIMPLE>
 __device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&pd)[(1 << LOGE) / 2], int t, int comp,
-                                         int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T g11, T g22,
-                                         T g12, T htau, T xang, int pieces, bool ymerge, T tm, T sm, T su, T sd,
+                                         int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T gh11, T gh22,
+                                         T gh12, T htau, T xang, int pieces, bool ymerge, T tm, T sm, T su, T sd,
                                          T (&nsum)[2]) {
   constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
 #pragma unroll
   for (int j = 0; j < H; ++j)
-    r_one<T, N, F, TIER>(pu[j], pd[j], t + (j + comp * H) * TT, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces,
-                         ymerge, tm, sm, su, sd, nsum);
+    r_one<T, N, F, TIER, SIMPLE>(pu[j], pd[j], t + (j + comp * H) * TT, y, tab, ty, p2, gh11, gh22, gh12, htau, xang,
+                                 pieces, ymerge, tm, sm, su, sd, nsum);
 }
 
 // Row-pass compute on registers already loaded: v holds this thread's
@@ -425,6 +422,7 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     const T g11 = gp[0], g22 = gp[1], g12 = gp[2];
     T htau, xang;
     if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
+    const T gh11 = htau * g11, gh22 = htau * g22, gh12 = htau * g12;
     const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
     const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
     T tm = T(0), sm = T(0);
@@ -460,19 +458,32 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     // interaction exponent is bounded; real time: the whole phase)
     const T hb = fabs(htau) * ((IMAG ? T(0) : gp[3]) + gmax * T(1.05) * rmax);
     const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
-    const bool tiny = !IMAG && __all_sync(mask, hb < T(0.015625));
-#define SPGPE_R_POINTS(TIER) \
-  r_points<T, LOGN, LOGE, F, TIER>(pu, pd, t, comp, y, tab, ty, p2, g11, g22, g12, htau, xang, pieces, ymerge, tm, sm, \
-                                   su, sd, nsum)
+    const bool tiny = __all_sync(mask, hb < (IMAG ? T(0.25) : T(0.015625)));
+    // the common layout (r_one's SIMPLE), decided for the whole warp
+    constexpr bool YM = !IMAG && (F & F_REND) && (F & F_RSTART);
+    const bool simple = __all_sync(mask, p2 == nullptr && (a.omega_pieces & 2) == 0 && (!YM || ymerge));
+#define SPGPE_R_POINTS(TIER, S)                                                                                     \
+  r_points<T, LOGN, LOGE, F, TIER, S>(pu, pd, t, comp, y, tab, ty, p2, gh11, gh22, gh12, htau, xang, pieces, ymerge, \
+                                      tm, sm, su, sd, nsum)
     if constexpr (sizeof(T) == 8) {
-      SPGPE_R_POINTS(2);
-    } else {
-      if (!IMAG && tiny)  // imaginary time has no tier 0
-        SPGPE_R_POINTS(0);
-      else if (small)
-        SPGPE_R_POINTS(1);
+      if (simple)
+        SPGPE_R_POINTS(2, true);
       else
-        SPGPE_R_POINTS(2);
+        SPGPE_R_POINTS(2, false);
+    } else if (simple) {
+      if (tiny)
+        SPGPE_R_POINTS(0, true);
+      else if (small)
+        SPGPE_R_POINTS(1, true);
+      else
+        SPGPE_R_POINTS(2, true);
+    } else {
+      if (tiny)
+        SPGPE_R_POINTS(0, false);
+      else if (small)
+        SPGPE_R_POINTS(1, false);
+      else
+        SPGPE_R_POINTS(2, false);
     }
 #undef SPGPE_R_POINTS
     // scatter back to one component per thread
@@ -876,8 +887,8 @@ __global__ void __launch_bounds__(256) ref_R_kernel(const RowArgs a) {
       vu *= exp(htau * q.x);
       vd *= exp(htau * q.y);
     } else {
-      vu += q.x;
-      vd += q.y;
+      vu = d_fma(htau, q.x, vu);
+      vd = d_fma(htau, q.y, vd);
     }
     q2z = q.z;
   }
@@ -886,7 +897,7 @@ __global__ void __launch_bounds__(256) ref_R_kernel(const RowArgs a) {
   const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
   cx<T> U = *u, D = *d;
   applyX<IMAG>(U, D, xc, pieces);
-  opD<IMAG>(U, D, vu, vd, gp[0], gp[1], gp[2], htau);
+  opD<IMAG>(U, D, vu, vd, htau * gp[0], htau * gp[1], htau * gp[2]);
   applyX<IMAG>(U, D, xc, pieces);
   *u = U;
   *d = D;

@@ -127,12 +127,18 @@ __host__ __device__ constexpr size_t rowu_smem(int n, int e, int es, int tw_entr
                                      (size_t)tw_entries * 16
                                : rowu_bytes(n, 1, es);
 }
-// Resident blocks the register budget is sized for: 24 warps per SM in single
-// precision, 16 in double precision.
+// Resident blocks the register budget is sized for: 24 warps per SM for
+// single-precision warp units, SPGPE_ROWB_THREADS_SP threads per SM for
+// single-precision block units (640: 96 registers a thread), 16 warps in
+// double precision.
+#ifndef SPGPE_ROWB_THREADS_SP
+#define SPGPE_ROWB_THREADS_SP 640
+#endif
 __host__ __device__ constexpr int rowu_min_blocks(int n, int e, int es) {
   return row_warp_local(n / e) && es == 8 ? SPGPE_ROWU_MINB
-         : (es == 8 ? 640 : 512) / rowu_block(n, e) > 0 ? (es == 8 ? 640 : 512) / rowu_block(n, e)
-                                                         : 1;
+         : (es == 8 ? SPGPE_ROWB_THREADS_SP : 512) / rowu_block(n, e) > 0
+             ? (es == 8 ? SPGPE_ROWB_THREADS_SP : 512) / rowu_block(n, e)
+             : 1;
 }
 
 template <class T, int LOGN, int LOGE, int F>

@@ -10,7 +10,8 @@ namespace {
 
 // fn: 0 expi2_m1 -> (wre, wim); 1 expm1_f -> (e); 2 expm1_small -> (e);
 // 3 shear_consts_2h (every tier, out of line) -> (t, s, neg);
-// 4 shear_consts_2h_small -> (t, s); 5 shear_consts_2h_tiny -> (t, s).
+// 4 shear_consts_2h_small -> (t, s); 5 shear_consts_2h_tiny -> (t, s);
+// 6 expm1_quarter -> (e).
 // out holds 3 floats per argument.
 __global__ void probe(int fn, const float *__restrict__ x, int n, float *__restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -28,6 +29,7 @@ __global__ void probe(int fn, const float *__restrict__ x, int n, float *__restr
       break;
     }
     case 4: spgpe::shear_consts_2h_small(h, a, b); break;
+    case 6: a = spgpe::expm1_quarter(h); break;
     default: spgpe::shear_consts_2h_tiny(h, a, b); break;
   }
   out[3 * i] = a;

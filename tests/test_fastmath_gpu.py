@@ -8,8 +8,8 @@ the GPU (a probe kernel built from the library's own header) at dense
 arguments up to the documented range and compares it with numpy's FP64
 functions of the same float arguments.  Bounds (the header's): exp(2ih) - 1
 within 2.5e-7 relative to |w|; expm1 within 1.5e-7 relative (expm1_small,
-below |x| = 1/2: 1e-7); the shear constants rotate a unit vector by 2h within
-3e-7.
+below |x| = 1/2: 1e-7; expm1_quarter, below |x| = 1/4: 1.5e-7); the shear
+constants rotate a unit vector by 2h within 3e-7.
 """
 import ctypes
 import os
@@ -123,6 +123,17 @@ def test_expm1_small(probe):
     ref = np.expm1(xd)
     err = np.abs(out[:, 0] - ref)
     assert np.all(err <= 1e-7 * np.abs(ref)), xd[np.argmax(err / np.abs(ref))]
+
+
+def test_expm1_quarter(probe):
+    """expm1 for |x| < 1/4 (the imaginary-time D factors of warps whose
+    interaction exponents are all below the bound): the series to x^6/6!,
+    truncation below 4.8e-8 relative."""
+    x = np.concatenate([np.linspace(-0.25, 0.25, 200001)[1:-1], logspace_both(-30, np.log10(0.249), 4001)])
+    xd, out = probe(6, x)
+    ref = np.expm1(xd)
+    err = np.abs(out[:, 0] - ref)
+    assert np.all(err <= 1.5e-7 * np.abs(ref)), xd[np.argmax(err / np.abs(ref))]
 
 
 def test_shear_constants_general_all_tiers(probe):
