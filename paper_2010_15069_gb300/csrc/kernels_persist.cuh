@@ -270,6 +270,14 @@ template <class T> __host__ __device__ constexpr int colp_cols_c(int logn, int l
   return c;
 }
 
+// Bytes of the column plan's twiddle table the persistent column pass keeps
+// in shared memory: the whole table when it fits in 16 KB (columns of up to
+// 1024 rows), else none (the table stays in global memory).
+template <class T> __host__ __device__ constexpr size_t colp_tw_bytes(int entries) {
+  return (size_t)entries * sizeof(typename TwType<T>::type) <= 16384 ? (size_t)entries * sizeof(typename TwType<T>::type)
+                                                                     : 0;
+}
+
 template <class T, int LOGN, int LOGE, bool IMAG, int C>
 __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     col_pass_p(const __grid_constant__ CUtensorMap map, const ColArgs a, int ntiles) {
@@ -279,8 +287,12 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
   constexpr int BOXH = N < 256 ? N : 256;  // rows per TMA box
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr size_t bufb = colp_buf_bytes(N, C, ES);
+  using TwT = typename TwType<T>::type;
+  constexpr int TWN = Plan<LOGN, LOGE>::entries();
+  constexpr size_t TWB = colp_tw_bytes<T>(TWN);
   cx<T> *btab = reinterpret_cast<cx<T> *>(smem_raw + kPipe * bufb);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(btab + N);
+  TwT *tws = reinterpret_cast<TwT *>(btab + N);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(tws) + TWB);
   const int c = threadIdx.x % C, t = threadIdx.x / C;
   const int cgroups = a.nx / C;
   const uint32_t tilebytes = (uint32_t)N * C * ES;
@@ -313,6 +325,11 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     if (nxt < ntiles) issue(nxt, 1);
   }
   for (int k = threadIdx.x; k < N; k += blockDim.x) btab[k] = reinterpret_cast<const cx<T> *>(a.kyt)[k];
+  const void *tw = a.tw;
+  if constexpr (TWB > 0) {
+    for (int k = threadIdx.x; k < TWN; k += blockDim.x) tws[k] = reinterpret_cast<const TwT *>(a.tw)[k];
+    tw = tws;
+  }
   __syncthreads();
 
   for (int i = 0; tile < ntiles; ++i) {
@@ -335,7 +352,7 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
     const cx<T> am = reinterpret_cast<const cx<T> *>(a.kxt)[(long)pc * a.nx + kx];
     __syncthreads();  // the dense tile is read; its space now serves the exchanges
     const ColAccC<T, C> acc{b + c};
-    col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, a.tw, am, btab, col_inv<T>(a, pc));
+    col_compute<T, LOGN, LOGE, IMAG>(v, t, acc, tw, am, btab, col_inv<T>(a, pc));
     cx<T> *col = reinterpret_cast<cx<T> *>(a.psi) + (long)pc * N * a.nx + kx;
     const int rs = TT * a.nx;
     const long cb = (long)pc * N * a.nx + kx, ct = (long)a.ninst * 2 * N * a.nx;
