@@ -382,17 +382,93 @@ __device__ __forceinline__ void r_one(cx<T> &u, cx<T> &d, int x, int y, const q4
   }
 }
 
-// R_end and/or R_start at this thread's H points (both components), as r_one.
-template <class T, int LOGN, int LOGE, int F, int TIER, bool SIMPLE>
-__device__ __forceinline__ void r_points(cx<T> (&pu)[(1 << LOGE) / 2], cx<T> (&pd)[(1 << LOGE) / 2], int t, int comp,
-                                         int y, const q4<T> *tab, const q4<T> &ty, const q4<T> *p2, T gh11, T gh22,
-                                         T gh12, T htau, T xang, int pieces, bool ymerge, T tm, T sm, T su, T sd,
-                                         T (&nsum)[2]) {
-  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E, H = E / 2;
+// R_end and/or R_start at this thread's K points (both components): pu[j],
+// pd[j] at x = t + (j + jo) * TT of row y; as r_one.
+template <class T, int LOGN, int LOGE, int F, int TIER, bool SIMPLE, int K>
+__device__ __forceinline__ void r_points(cx<T> (&pu)[K], cx<T> (&pd)[K], int t, int jo, int y, const q4<T> *tab,
+                                         const q4<T> &ty, const q4<T> *p2, T gh11, T gh22, T gh12, T htau, T xang,
+                                         int pieces, bool ymerge, T tm, T sm, T su, T sd, T (&nsum)[2]) {
+  constexpr int N = 1 << LOGN, E = 1 << LOGE, TT = N / E;
 #pragma unroll
-  for (int j = 0; j < H; ++j)
-    r_one<T, N, F, TIER, SIMPLE>(pu[j], pd[j], t + (j + comp * H) * TT, y, tab, ty, p2, gh11, gh22, gh12, htau, xang,
+  for (int j = 0; j < K; ++j)
+    r_one<T, N, F, TIER, SIMPLE>(pu[j], pd[j], t + (j + jo) * TT, y, tab, ty, p2, gh11, gh22, gh12, htau, xang,
                                  pieces, ymerge, tm, sm, su, sd, nsum);
+}
+
+// The pointwise part of the row pass, R_end and/or R_start, on K points per
+// thread with both components in registers (pu[j], pd[j] at x = t + (j + jo)
+// * TT of row y).  The lanes in mask hold together the points whose phase
+// bound picks one series tier for all of them (the same point sets in every
+// variant of the pass, so that they round alike).  Adds the thread's
+// atom-number partials of the R_end result to nsum when F has F_PART.
+template <class T, int LOGN, int LOGE, int F, int K>
+__device__ __forceinline__ void r_apply(cx<T> (&pu)[K], cx<T> (&pd)[K], int t, int jo, unsigned mask, int inst, int y,
+                                        const q4<T> *tab, const RowArgs &a, T (&nsum)[2]) {
+  constexpr bool IMAG = (F & F_IMAG) != 0;
+  // (bounds-checked build: a bad row index is recorded and replaced by 0, so
+  // that every thread still reaches the warp's barriers)
+  const long tyi = in_bounds(a.flags, (long)inst * a.ny + y, (long)a.ninst * a.ny) ? (long)inst * a.ny + y : 0;
+  const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[tyi];
+  const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
+  const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
+  const T g11 = gp[0], g22 = gp[1], g12 = gp[2];
+  T htau, xang;
+  if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
+  const T gh11 = htau * g11, gh22 = htau * g22, gh12 = htau * g12;
+  const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
+  const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
+  T tm = T(0), sm = T(0);
+  T su = T(1), sd = T(1);
+  if constexpr ((F & F_LAG) != 0) {
+    su = reinterpret_cast<const T *>(a.scale_pred_t)[2 * inst];
+    sd = reinterpret_cast<const T *>(a.scale_pred_t)[2 * inst + 1];
+  }
+  bool ymerge = false;
+  if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
+  // One phase tier per lane group: the shortest series whose range holds
+  // |htau e| at every point of the group.  e <= Vb + G rho_tot with Vb = max
+  // |V +- delta/2| of the instance and G = max(|g11|, |g22|) + |g12|;
+  // rho_tot = |u|^2 + |d|^2 at a point is left unchanged by real-time R (5 %
+  // margin for the imaginary-time X).
+  T rmax = T(0);
+#pragma unroll
+  for (int j = 0; j < K; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
+                                                    d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
+  // (the lagged pass scales the densities between R_end and R_start by the
+  // squared predicted scale)
+  if constexpr ((F & F_LAG) != 0) rmax *= fmax(T(1), fmax(su * su, sd * sd));
+  // (imaginary time: the potential factors come from tables, so only the
+  // interaction exponent is bounded; real time: the whole phase)
+  const T hb = fabs(htau) * ((IMAG ? T(0) : gp[3]) + gmax * T(1.05) * rmax);
+  const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
+  const bool tiny = __all_sync(mask, hb < (IMAG ? T(0.25) : T(0.015625)));
+  // the common layout (r_one's SIMPLE), decided for the whole group
+  constexpr bool YM = !IMAG && (F & F_REND) && (F & F_RSTART);
+  const bool simple = __all_sync(mask, p2 == nullptr && (a.omega_pieces & 2) == 0 && (!YM || ymerge));
+#define SPGPE_R_POINTS(TIER, S)                                                                                      \
+  r_points<T, LOGN, LOGE, F, TIER, S, K>(pu, pd, t, jo, y, tab, ty, p2, gh11, gh22, gh12, htau, xang, pieces, ymerge, \
+                                         tm, sm, su, sd, nsum)
+  if constexpr (sizeof(T) == 8) {
+    if (simple)
+      SPGPE_R_POINTS(2, true);
+    else
+      SPGPE_R_POINTS(2, false);
+  } else if (simple) {
+    if (tiny)
+      SPGPE_R_POINTS(0, true);
+    else if (small)
+      SPGPE_R_POINTS(1, true);
+    else
+      SPGPE_R_POINTS(2, true);
+  } else {
+    if (tiny)
+      SPGPE_R_POINTS(0, false);
+    else if (small)
+      SPGPE_R_POINTS(1, false);
+    else
+      SPGPE_R_POINTS(2, false);
+  }
+#undef SPGPE_R_POINTS
 }
 
 // Row-pass compute on registers already loaded: v holds this thread's
@@ -405,7 +481,6 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
                                             int inst, int y, const Acc &acc, const q4<T> *tab,
                                             const RowArgs &a, T (&nsum)[2]) {
   constexpr int E = 1 << LOGE, H = E / 2;
-  constexpr bool IMAG = (F & F_IMAG) != 0;
   if constexpr (F & F_IFFT) block_fft<LOGN, LOGE, +1, 1>(v, t, a.tw, acc);
   if constexpr (F & F_SCALE) {
     const T sc = reinterpret_cast<const T *>(a.scale_t)[2 * inst + comp];
@@ -413,31 +488,6 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
     for (int m = 0; m < E; ++m) v[0][m] = cscale(v[0][m], sc);
   }
   if constexpr (F & (F_REND | F_RSTART)) {
-    // (bounds-checked build: a bad row index is recorded and replaced by 0, so
-    // that every thread still reaches the warp's barriers)
-    const long tyi = in_bounds(a.flags, (long)inst * a.ny + y, (long)a.ninst * a.ny) ? (long)inst * a.ny + y : 0;
-    const q4<T> ty = reinterpret_cast<const q4<T> *>(a.taby)[tyi];
-    const q4<T> *p2 = reinterpret_cast<const q4<T> *>(a.pot2d);
-    const T *gp = reinterpret_cast<const T *>(a.gparT) + 4 * inst;
-    const T g11 = gp[0], g22 = gp[1], g12 = gp[2];
-    T htau, xang;
-    if constexpr (sizeof(T) == 4) { htau = a.htau_f; xang = a.xang_f; } else { htau = a.htau_d; xang = a.xang; }
-    const T gh11 = htau * g11, gh22 = htau * g22, gh12 = htau * g12;
-    const int pieces = (a.omega_pieces & 3) | (p2 ? 4 : 0);
-    const T gmax = fmax(fabs(g11), fabs(g22)) + fabs(g12);
-    T tm = T(0), sm = T(0);
-    T su = T(1), sd = T(1);
-    if constexpr ((F & F_LAG) != 0) {
-      su = reinterpret_cast<const T *>(a.scale_pred_t)[2 * inst];
-      sd = reinterpret_cast<const T *>(a.scale_pred_t)[2 * inst + 1];
-    }
-    bool ymerge = false;
-    if constexpr (!IMAG && (F & F_REND) && (F & F_RSTART)) ymerge = x_double(ty.z, ty.w, tm, sm);
-    // One phase tier per warp: the shortest series whose range holds |htau e|
-    // at every point of the warp.  e <= Vb + G rho_tot with Vb = max |V +-
-    // delta/2| of the instance and G = max(|g11|, |g22|) + |g12|; rho_tot =
-    // |u|^2 + |d|^2 at a point is left unchanged by real-time R (5 % margin
-    // for the imaginary-time X).
     // gather: (pu[j], pd[j]) = both components at position m = j + comp*H
     cx<T> pu[H], pd[H];
 #pragma unroll
@@ -447,45 +497,7 @@ __device__ __forceinline__ void row_compute(cx<T> (&v)[1][1 << LOGE], int t, int
       pu[j] = comp ? rcv : v[0][j];
       pd[j] = comp ? v[0][H + j] : rcv;
     }
-    T rmax = T(0);
-#pragma unroll
-    for (int j = 0; j < H; ++j) rmax = fmax(rmax, d_fma(pu[j].re, pu[j].re, pu[j].im * pu[j].im) +
-                                                      d_fma(pd[j].re, pd[j].re, pd[j].im * pd[j].im));
-    // (the lagged pass scales the densities between R_end and R_start by the
-    // squared predicted scale)
-    if constexpr ((F & F_LAG) != 0) rmax *= fmax(T(1), fmax(su * su, sd * sd));
-    // (imaginary time: the potential factors come from tables, so only the
-    // interaction exponent is bounded; real time: the whole phase)
-    const T hb = fabs(htau) * ((IMAG ? T(0) : gp[3]) + gmax * T(1.05) * rmax);
-    const bool small = __all_sync(mask, hb < (IMAG ? T(0.5) : T(0.125)));
-    const bool tiny = __all_sync(mask, hb < (IMAG ? T(0.25) : T(0.015625)));
-    // the common layout (r_one's SIMPLE), decided for the whole warp
-    constexpr bool YM = !IMAG && (F & F_REND) && (F & F_RSTART);
-    const bool simple = __all_sync(mask, p2 == nullptr && (a.omega_pieces & 2) == 0 && (!YM || ymerge));
-#define SPGPE_R_POINTS(TIER, S)                                                                                     \
-  r_points<T, LOGN, LOGE, F, TIER, S>(pu, pd, t, comp, y, tab, ty, p2, gh11, gh22, gh12, htau, xang, pieces, ymerge, \
-                                      tm, sm, su, sd, nsum)
-    if constexpr (sizeof(T) == 8) {
-      if (simple)
-        SPGPE_R_POINTS(2, true);
-      else
-        SPGPE_R_POINTS(2, false);
-    } else if (simple) {
-      if (tiny)
-        SPGPE_R_POINTS(0, true);
-      else if (small)
-        SPGPE_R_POINTS(1, true);
-      else
-        SPGPE_R_POINTS(2, true);
-    } else {
-      if (tiny)
-        SPGPE_R_POINTS(0, false);
-      else if (small)
-        SPGPE_R_POINTS(1, false);
-      else
-        SPGPE_R_POINTS(2, false);
-    }
-#undef SPGPE_R_POINTS
+    r_apply<T, LOGN, LOGE, F, H>(pu, pd, t, comp * H, mask, inst, y, tab, a, nsum);
     // scatter back to one component per thread
 #pragma unroll
     for (int j = 0; j < H; ++j) {
