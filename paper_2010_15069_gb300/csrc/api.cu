@@ -912,6 +912,77 @@ template <class F> int for_classes(spgpe_ctx *c, const void *psi, bool write_bac
   return SPGPE_OK;
 }
 
+// Host spinor of a multi-size batch: each class's instances go through in
+// chunks as in host_pipeline, the copies on the batch's two copy streams and
+// the steps on the class's own stream, so that the copies of one chunk
+// overlap the steps of the chunks and classes queued before it.
+// run(k, i0, ni, base) queues the steps of instances i0 .. i0 + ni - 1 of
+// class k (in the class's own numbering) of the class spinor at `base` on the
+// class's stream.  Synchronises; sums the classes' launch counts.
+template <class F> int host_pipeline_multi(spgpe_ctx *c, void *psi, F &&run) {
+  int r = dev_alloc(c, &c->d_stage, c->psi_bytes());
+  if (r) return r;
+  if (!c->cp_in) {
+    CK(c, cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
+    CK(c, cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
+  }
+  std::vector<int> nch(c->cls.size());
+  int total = 0;
+  for (size_t k = 0; k < c->cls.size(); ++k) total += (nch[k] = std::min(c->cls[k]->ninst, c->host_chunks));
+  while ((int)c->ev_in.size() < total + 1) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(c, cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    CK(c, cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    c->ev_in.push_back(a);
+    c->ev_done.push_back(b);
+  }
+  // the copies start after the work already queued on the batch's stream
+  CK(c, cudaEventRecord(c->ev_done[total], c->st));
+  CK(c, cudaStreamWaitEvent(c->cp_in, c->ev_done[total], 0));
+  unsigned char *dev = static_cast<unsigned char *>(c->d_stage), *hst = static_cast<unsigned char *>(psi);
+  int launches = 0;
+  for (size_t k = 0, e = 0; k < c->cls.size(); ++k) {
+    spgpe_ctx *ck = c->cls[k];
+    ck->last_launches = 0;
+    const size_t per = 2 * (size_t)ck->plane() * ck->es;
+    for (int j = 0; j < nch[k]; ++j, ++e) {
+      const int i0 = (int)((long)j * ck->ninst / nch[k]), i1 = (int)((long)(j + 1) * ck->ninst / nch[k]);
+      const size_t off = c->cls_off[k] + (size_t)i0 * per, bytes = (size_t)(i1 - i0) * per;
+      CK(c, cudaMemcpyAsync(dev + off, hst + off, bytes, cudaMemcpyHostToDevice, c->cp_in));
+      CK(c, cudaEventRecord(c->ev_in[e], c->cp_in));
+      CK(c, cudaStreamWaitEvent(ck->st, c->ev_in[e], 0));
+      if ((r = run((int)k, i0, i1 - i0, dev + c->cls_off[k]))) return class_fail(c, ck, r);
+      CK(c, cudaEventRecord(c->ev_done[e], ck->st));
+      CK(c, cudaStreamWaitEvent(c->cp_out, c->ev_done[e], 0));
+      CK(c, cudaMemcpyAsync(hst + off, dev + off, bytes, cudaMemcpyDeviceToHost, c->cp_out));
+    }
+    launches += ck->last_launches;
+  }
+  CK(c, cudaStreamSynchronize(c->cp_out));
+  for (spgpe_ctx *k : c->cls) CK(c, cudaStreamSynchronize(k->st));
+  c->last_launches = launches;
+  for (spgpe_ctx *k : c->cls)
+    if ((r = read_flags(k))) return class_fail(c, k, r);
+  return SPGPE_OK;
+}
+
+// Real-time steps of instances i0 .. i0 + ni - 1 of the batch at p, queued
+// on the context's stream.
+int real_enqueue(spgpe_ctx *c, void *p, double dt, int nsteps, int i0, int ni) {
+  int r = ensure_tables(c, dt, 0);
+  if (r) return r;
+  RowArgs ra = row_args(c, p, dt);
+  ColArgs ca = col_args(c, p);
+  restrict_row(c, ra, i0, ni);
+  restrict_col(c, ca, i0, ni);
+  CK(c, row(c, kRealFirst, ra));
+  for (int s = 1; s <= nsteps; ++s) {
+    CK(c, col(c, false, ca));
+    CK(c, row(c, s < nsteps ? kRealMid : kRealLast, ra));
+  }
+  return SPGPE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1112,6 +1183,10 @@ int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
     if (!psi || nsteps < 0 || !std::isfinite(dt)) return fail(c, SPGPE_EINVAL, "bad psi, dt or nsteps");
     int r = check_ready(c);
     if (r) return r;
+    if (nsteps > 0 && !is_device_ptr(psi))
+      return host_pipeline_multi(c, psi, [&](int k, int i0, int ni, void *p) {
+        return real_enqueue(c->cls[k], p, dt, nsteps, i0, ni);
+      });
     return for_classes(c, psi, true, [&](spgpe_ctx *k, void *p, int) { return spgpe_step_real(k, p, dt, nsteps); });
   }
   int r = check_ready(c);
@@ -1121,18 +1196,7 @@ int spgpe_step_real(spgpe_ctx *c, void *psi, double dt, int nsteps) {
   if (nsteps == 0) return SPGPE_OK;
   if ((r = ensure_tables(c, dt, 0))) return r;
   // the steps of instances i0 .. i0 + ni - 1 of the batch at p
-  auto run = [&](int i0, int ni, void *p) -> int {
-    RowArgs ra = row_args(c, p, dt);
-    ColArgs ca = col_args(c, p);
-    restrict_row(c, ra, i0, ni);
-    restrict_col(c, ca, i0, ni);
-    CK(c, row(c, kRealFirst, ra));
-    for (int s = 1; s <= nsteps; ++s) {
-      CK(c, col(c, false, ca));
-      CK(c, row(c, s < nsteps ? kRealMid : kRealLast, ra));
-    }
-    return SPGPE_OK;
-  };
+  auto run = [&](int i0, int ni, void *p) -> int { return real_enqueue(c, p, dt, nsteps, i0, ni); };
   if (!is_device_ptr(psi)) {
     if ((r = host_pipeline(c, psi, run))) return r;
     return read_flags(c);
@@ -1159,6 +1223,10 @@ int spgpe_step_imag(spgpe_ctx *c, void *psi, double dtau, int nsteps, int norm_m
         for (int i = 0; i < c->ninst; ++i) residual_out[i] = NAN;
       return SPGPE_OK;
     }
+    if (!residual_out && !is_device_ptr(psi))
+      return host_pipeline_multi(c, psi, [&](int k, int i0, int ni, void *p) {
+        return imag_enqueue(c->cls[k], p, dtau, nsteps, norm_mode, t0, t1, false, i0, ni, lagged);
+      });
     // queue every class before reading any residual, so the classes overlap
     r = for_classes(c, psi, true, [&](spgpe_ctx *k, void *p, int) {
       k->last_launches = 0;

@@ -105,6 +105,27 @@ def test_multi_size_relaxation_and_host_spinors():
     assert (res <= 1e-8).sum() >= len(insts) // 2
 
 
+@pytest.mark.parametrize("dtype,chunks", [("c64", "1"), ("c64", "3"), ("c128", "8")])
+def test_multi_size_host_spinors_go_through_in_chunks_with_the_same_bits(dtype, chunks, monkeypatch):
+    """A host spinor of a multi-size batch goes through each class in chunks
+    of instances (SPGPE_HOST_CHUNKS per class), copies overlapping the other
+    chunks' steps: real time, exact and lagged imaginary time end with the
+    bits of the same steps on a device spinor."""
+    monkeypatch.setenv("SPGPE_HOST_CHUNKS", chunks)
+    insts = instances()
+    npt = NPT[dtype]
+    with sp.Context.multi(CLASSES, dtype) as c:
+        set_all(c, insts, True)
+        host = np.concatenate([x[3].astype(npt).ravel() for x in insts])
+        d = torch.from_numpy(host.copy()).cuda()
+        for call in (lambda x: c.step_real(x, 1e-3, 5), lambda x: c.step_imag(x, 1e-3, 1),
+                     lambda x: c.step_imag(x, 1e-3, 7, sp.SPGPE_NORM_PER_COMPONENT, (0.6, 0.4)),
+                     lambda x: c.step_imag(x, 1e-3, 6, lagged=True)):
+            call(host)
+            call(d)
+            assert np.array_equal(d.cpu().numpy(), host)
+
+
 def test_autotune_picks_a_variant_per_class_and_leaves_psi_alone():
     insts = instances()
     with sp.Context.multi(CLASSES, "c64") as c:
