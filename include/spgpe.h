@@ -168,7 +168,8 @@ int spgpe_step_imag(spgpe_ctx *ctx, void *psi, double dtau, int nsteps, int norm
  *   complex64 until every residual is <= max(tol, handoff), or, with
  *   handoff = 0, until each instance's residual has reached complex64's
  *   rounding floor (below 2^-18 / dtau) and improves by less than a fifth per
- *   chunk; then widened back into psi and relaxed in complex128 to tol.  The
+ *   chunk (an instance at the floor is stepped on until the last one gets
+ *   there); then widened back into psi and relaxed in complex128 to tol.  The
  *   two stages share max_steps: the complex128 stage runs at most max_steps
  *   minus the steps the complex64 stage ran.  The rounding of every complex64 step
  *   also excites slowly relaxing modes that a smooth initial state leaves

@@ -1522,9 +1522,11 @@ struct Member {
 // The members' chunks are queued on their own streams before any residual is
 // read, so size classes run side by side.  An instance that is done is frozen
 // (the passes skip it) while the others go on; its residual stays the last
-// one measured.  to_floor: an instance is also done once its residual has
-// reached the rounding floor of complex64 (below 2^-18 / dtau) and improves by
-// less than a fifth from one chunk to the next.  give_up: an instance is also
+// one measured.  to_floor: an instance also stops holding the stage open once
+// its residual has reached the rounding floor of complex64 (below 2^-18 /
+// dtau) and improves by less than a fifth from one chunk to the next, but is
+// stepped on until the stage ends (its slow modes keep relaxing; the stage
+// budget is shared with the next one).  give_up: an instance is also
 // done once its smallest residual so far has not halved in kStallChecks
 // chunks (a metastable state, or a relaxation far too slow for the budget).
 constexpr int kStallChecks = 40;
@@ -1533,6 +1535,7 @@ int relax_stage(spgpe_ctx *owner, std::vector<Member> &mem, int ntotal, double d
                 std::vector<double> &res, int *steps, int *launches) {
   const double floor64 = std::ldexp(1.0, -18) / dtau;
   std::vector<int> act((size_t)ntotal, 1), since((size_t)ntotal, 0);
+  std::vector<char> counted((size_t)ntotal, 0);  // no longer holding the stage open
   std::vector<double> prev((size_t)ntotal, INFINITY), best((size_t)ntotal, INFINITY), r((size_t)ntotal);
   int done = 0, nact = ntotal;
   auto upload_mask = [&](const Member &m) {
@@ -1643,10 +1646,18 @@ int relax_stage(spgpe_ctx *owner, std::vector<Member> &mem, int ntotal, double d
         } else {
           ++since[i];
         }
-        if (v <= tol || (to_floor && v < floor64 && v > 0.8 * prev[i]) || (give_up && since[i] >= kStallChecks)) {
+        if (v <= tol || (give_up && since[i] >= kStallChecks)) {
           act[i] = 0;
-          --nact;
           changed[k] = 1;
+          if (!counted[i]) {
+            counted[i] = 1;
+            --nact;
+          }
+        } else if (to_floor && !counted[i] && v < floor64 && v > 0.8 * prev[i]) {
+          // at the floor: done for this stage, but stepped on while the stage
+          // lasts (cheap in complex64), so that its slow modes keep relaxing
+          counted[i] = 1;
+          --nact;
         }
         prev[i] = v;
       }
