@@ -271,11 +271,16 @@ template <class T> __host__ __device__ constexpr int colp_cols_c(int logn, int l
 }
 
 // Bytes of the column plan's twiddle table the persistent column pass keeps
-// in shared memory: the whole table when it fits in 16 KB (columns of up to
-// 1024 rows), else none (the table stays in global memory).
-template <class T> __host__ __device__ constexpr size_t colp_tw_bytes(int entries) {
-  return (size_t)entries * sizeof(typename TwType<T>::type) <= 16384 ? (size_t)entries * sizeof(typename TwType<T>::type)
-                                                                     : 0;
+// in shared memory: the whole table when the block's shared memory (two tile
+// buffers, the K table, the table, the barriers) stays within a block's
+// limit (in complex64 columns of up to 2048 rows), else none (the table
+// stays in global memory).
+template <class T> __host__ __device__ constexpr size_t colp_tw_bytes(int logn, int c, int entries) {
+  return kPipe * colp_buf_bytes(1 << logn, c, (int)sizeof(cx<T>)) + ((size_t)1 << logn) * sizeof(cx<T>) +
+                     (size_t)entries * sizeof(typename TwType<T>::type) + kPipe * sizeof(uint64_t) <=
+                 kMaxSmemPerBlock
+             ? (size_t)entries * sizeof(typename TwType<T>::type)
+             : 0;
 }
 
 template <class T, int LOGN, int LOGE, bool IMAG, int C>
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(LOGN <= 8 ? 256 : 512, LOGN <= 8 ? 2 : 1)
   constexpr size_t bufb = colp_buf_bytes(N, C, ES);
   using TwT = typename TwType<T>::type;
   constexpr int TWN = Plan<LOGN, LOGE>::entries();
-  constexpr size_t TWB = colp_tw_bytes<T>(TWN);
+  constexpr size_t TWB = colp_tw_bytes<T>(LOGN, C, TWN);
   cx<T> *btab = reinterpret_cast<cx<T> *>(smem_raw + kPipe * bufb);
   TwT *tws = reinterpret_cast<TwT *>(btab + N);
   uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(tws) + TWB);

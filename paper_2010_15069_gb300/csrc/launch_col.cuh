@@ -160,7 +160,7 @@ cudaError_t colp_launch_n(ColArgs a, const CUtensorMap &map, cudaStream_t st, in
   const int threads = C * TT;
   const int es = sizeof(cx<T>);
   const size_t smem = kPipe * colp_buf_bytes(N, C, es) + (size_t)N * es +
-                      colp_tw_bytes<T>(Plan<LOGN, LOGE>::entries()) + kPipe * sizeof(uint64_t);
+                      colp_tw_bytes<T>(LOGN, C, Plan<LOGN, LOGE>::entries()) + kPipe * sizeof(uint64_t);
   if (smem > kMaxSmemPerBlock) return cudaErrorNotSupported;  // caller falls back to the plain pass
   static int granted = 0;
   cudaError_t e = grant_smem_c(kern, smem, granted);
