@@ -374,8 +374,8 @@ def warm_states(f, probs):
 
 def ground_state_verdict(psi_a, psi_b, e_a, e_b, res_a, res_b, tol, gap_est=0.1, e_tol=1e-5):
     """The comparison of two relaxed ground states of the same problem
-    (metastable states may legitimately differ between two
-    runs): 'match' when both residuals are within tol and the states agree up
+    (imaginary time can end on different metastable states of nearly equal
+    energy from two starts): 'match' when both residuals are within tol and the states agree up
     to the global phase within tol / gap_est (the distance to the fixed point
     that a residual of tol allows for a slowest relaxation rate gap_est);
     'degenerate' when the energies agree within e_tol (relative) but the

@@ -1,4 +1,4 @@
-// Microbenchmarks of the ceilings the kernels are judged against: FP32 and
+// Microbenchmarks of the ceilings the kernels are measured against: FP32 and
 // FP64 fused multiply-add throughput, sincosf throughput, read bandwidth over
 // working sets from a few MB to well above the L2 size (the bandwidth step
 // shows the L2 capacity), and the HBM copy bandwidth.  They only launch

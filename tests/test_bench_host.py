@@ -37,9 +37,9 @@ def test_oracle_pool_uses_every_core(orc):
 
 
 def test_ground_state_verdict():
-    """two relaxed states of one problem 'match' when both are
-    converged and agree up to the global phase, are 'degenerate' when only
-    their energies agree, and a 'mismatch' otherwise."""
+    """Two relaxed states of one problem 'match' when both are converged and
+    agree up to the global phase, are 'degenerate' when only their energies
+    agree (different metastable states), and a 'mismatch' otherwise."""
     import numpy as np
     import bench
     rng = np.random.default_rng(0)

@@ -1,7 +1,7 @@
 """The bounds-checked build (libspgpe_bounds.so, -DSPGPE_BOUNDS) against the
 release build, bit for bit.
 
-compute-sanitizer is closed on this machine; its stand-in is a build whose
+The stand-in for a memory checker is a build whose
 kernels check every global index of the step passes (spinor loads and stores,
 the bulk-copy and TMA boxes, the step tables, the atom-number partials)
 against its buffer, record an index outside it as SPGPE_EBOUNDS and skip the
