@@ -615,21 +615,33 @@ template <class F> int host_pipeline(spgpe_ctx *c, void *psi, F &&run) {
     c->ev_in.push_back(a);
     c->ev_done.push_back(b);
   }
-  // the copies start after the work already queued on the context's stream
-  CK(c, cudaEventRecord(c->ev_done[nch], c->st));
-  CK(c, cudaStreamWaitEvent(c->cp_in, c->ev_done[nch], 0));
   const size_t per = 2 * (size_t)c->plane() * c->es;
   unsigned char *dev = static_cast<unsigned char *>(c->d_stage), *hst = static_cast<unsigned char *>(psi);
-  for (int k = 0; k < nch; ++k) {
-    const int i0 = (int)((long)k * c->ninst / nch), i1 = (int)((long)(k + 1) * c->ninst / nch);
-    const size_t off = (size_t)i0 * per, bytes = (size_t)(i1 - i0) * per;
-    CK(c, cudaMemcpyAsync(dev + off, hst + off, bytes, cudaMemcpyHostToDevice, c->cp_in));
-    CK(c, cudaEventRecord(c->ev_in[k], c->cp_in));
-    CK(c, cudaStreamWaitEvent(c->st, c->ev_in[k], 0));
-    if ((r = run(i0, i1 - i0, c->d_stage))) return r;
-    CK(c, cudaEventRecord(c->ev_done[k], c->st));
-    CK(c, cudaStreamWaitEvent(c->cp_out, c->ev_done[k], 0));
-    CK(c, cudaMemcpyAsync(hst + off, dev + off, bytes, cudaMemcpyDeviceToHost, c->cp_out));
+  auto queue = [&]() -> int {
+    // the copies start after the work already queued on the context's stream
+    CK(c, cudaEventRecord(c->ev_done[nch], c->st));
+    CK(c, cudaStreamWaitEvent(c->cp_in, c->ev_done[nch], 0));
+    for (int k = 0; k < nch; ++k) {
+      const int i0 = (int)((long)k * c->ninst / nch), i1 = (int)((long)(k + 1) * c->ninst / nch);
+      const size_t off = (size_t)i0 * per, bytes = (size_t)(i1 - i0) * per;
+      CK(c, cudaMemcpyAsync(dev + off, hst + off, bytes, cudaMemcpyHostToDevice, c->cp_in));
+      CK(c, cudaEventRecord(c->ev_in[k], c->cp_in));
+      CK(c, cudaStreamWaitEvent(c->st, c->ev_in[k], 0));
+      int rr = run(i0, i1 - i0, c->d_stage);
+      if (rr) return rr;
+      CK(c, cudaEventRecord(c->ev_done[k], c->st));
+      CK(c, cudaStreamWaitEvent(c->cp_out, c->ev_done[k], 0));
+      CK(c, cudaMemcpyAsync(hst + off, dev + off, bytes, cudaMemcpyDeviceToHost, c->cp_out));
+    }
+    return SPGPE_OK;
+  };
+  if ((r = queue())) {
+    // copies already queued still use the caller's buffer: let them finish
+    cudaStreamSynchronize(c->cp_in);
+    cudaStreamSynchronize(c->cp_out);
+    cudaStreamSynchronize(c->st);
+    cudaGetLastError();
+    return r;
   }
   CK(c, cudaStreamSynchronize(c->cp_out));
   CK(c, cudaStreamSynchronize(c->st));
@@ -936,27 +948,39 @@ template <class F> int host_pipeline_multi(spgpe_ctx *c, void *psi, F &&run) {
     c->ev_in.push_back(a);
     c->ev_done.push_back(b);
   }
-  // the copies start after the work already queued on the batch's stream
-  CK(c, cudaEventRecord(c->ev_done[total], c->st));
-  CK(c, cudaStreamWaitEvent(c->cp_in, c->ev_done[total], 0));
   unsigned char *dev = static_cast<unsigned char *>(c->d_stage), *hst = static_cast<unsigned char *>(psi);
   int launches = 0;
-  for (size_t k = 0, e = 0; k < c->cls.size(); ++k) {
-    spgpe_ctx *ck = c->cls[k];
-    ck->last_launches = 0;
-    const size_t per = 2 * (size_t)ck->plane() * ck->es;
-    for (int j = 0; j < nch[k]; ++j, ++e) {
-      const int i0 = (int)((long)j * ck->ninst / nch[k]), i1 = (int)((long)(j + 1) * ck->ninst / nch[k]);
-      const size_t off = c->cls_off[k] + (size_t)i0 * per, bytes = (size_t)(i1 - i0) * per;
-      CK(c, cudaMemcpyAsync(dev + off, hst + off, bytes, cudaMemcpyHostToDevice, c->cp_in));
-      CK(c, cudaEventRecord(c->ev_in[e], c->cp_in));
-      CK(c, cudaStreamWaitEvent(ck->st, c->ev_in[e], 0));
-      if ((r = run((int)k, i0, i1 - i0, dev + c->cls_off[k]))) return class_fail(c, ck, r);
-      CK(c, cudaEventRecord(c->ev_done[e], ck->st));
-      CK(c, cudaStreamWaitEvent(c->cp_out, c->ev_done[e], 0));
-      CK(c, cudaMemcpyAsync(hst + off, dev + off, bytes, cudaMemcpyDeviceToHost, c->cp_out));
+  auto queue = [&]() -> int {
+    // the copies start after the work already queued on the batch's stream
+    CK(c, cudaEventRecord(c->ev_done[total], c->st));
+    CK(c, cudaStreamWaitEvent(c->cp_in, c->ev_done[total], 0));
+    for (size_t k = 0, e = 0; k < c->cls.size(); ++k) {
+      spgpe_ctx *ck = c->cls[k];
+      ck->last_launches = 0;
+      const size_t per = 2 * (size_t)ck->plane() * ck->es;
+      for (int j = 0; j < nch[k]; ++j, ++e) {
+        const int i0 = (int)((long)j * ck->ninst / nch[k]), i1 = (int)((long)(j + 1) * ck->ninst / nch[k]);
+        const size_t off = c->cls_off[k] + (size_t)i0 * per, bytes = (size_t)(i1 - i0) * per;
+        CK(c, cudaMemcpyAsync(dev + off, hst + off, bytes, cudaMemcpyHostToDevice, c->cp_in));
+        CK(c, cudaEventRecord(c->ev_in[e], c->cp_in));
+        CK(c, cudaStreamWaitEvent(ck->st, c->ev_in[e], 0));
+        const int rr = run((int)k, i0, i1 - i0, dev + c->cls_off[k]);
+        if (rr) return class_fail(c, ck, rr);
+        CK(c, cudaEventRecord(c->ev_done[e], ck->st));
+        CK(c, cudaStreamWaitEvent(c->cp_out, c->ev_done[e], 0));
+        CK(c, cudaMemcpyAsync(hst + off, dev + off, bytes, cudaMemcpyDeviceToHost, c->cp_out));
+      }
+      launches += ck->last_launches;
     }
-    launches += ck->last_launches;
+    return SPGPE_OK;
+  };
+  if ((r = queue())) {
+    // copies already queued still use the caller's buffer: let them finish
+    cudaStreamSynchronize(c->cp_in);
+    cudaStreamSynchronize(c->cp_out);
+    for (spgpe_ctx *k : c->cls) cudaStreamSynchronize(k->st);
+    cudaGetLastError();
+    return r;
   }
   CK(c, cudaStreamSynchronize(c->cp_out));
   for (spgpe_ctx *k : c->cls) CK(c, cudaStreamSynchronize(k->st));
